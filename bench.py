@@ -1,0 +1,352 @@
+"""Benchmark of the Quantization Tree forward step (Algorithm III of Pages &
+Wilbertz, arXiv:1101.3228) on GB300.
+
+Metric: certified sample.layers/s -- M pairs per layer times n layers divided
+by the device time of one qt_transitions call (counts exact under the FP64
+contract, ready on the device).  A step is one whole forward step over all
+layers.  Default workload: the 2-factor OU model (d = 2, n = 100 daily layers,
+N_k = 500 product grids, M = 10^7 pairs per layer).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  With torchrun, every rank runs an independent
+replica with its own seed (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import qt_workloads as W  # noqa: E402
+
+FP32_LANES_PER_SM = 128
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="ou2", choices=list(W.BUILDERS))
+    ap.add_argument("--form", default="auto")
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--M", type=int, default=0, help="override samples per layer")
+    return ap.parse_args()
+
+
+def workload(name, M=0):
+    model = W.get(name)
+    if M:
+        model = W.get(name, M=M) if name != "paper" else W.paper(M=M)
+    return model
+
+
+def grid_method(model):
+    from paper_1101_3228_gb300 import binding as B
+    return {"lloyd1d": B.GRID_LLOYD1D, "product": B.GRID_PRODUCT, "kmeans": B.GRID_KMEANS}[model.grid_kind]
+
+
+def default_form(model, B):
+    return B.FORM_PLAIN_F64 if model.name == "bs1d" else B.FORM_F32_RECHECK
+
+
+def plain_form(model, B):
+    # the plain GPU comparator: exact FP64 brute force for d <= 2, FP32 brute force
+    # with FP64 recheck for d >= 4 (the path the learned and tensor forms are judged against)
+    return B.FORM_PLAIN_F64 if model.d <= 2 else B.FORM_F32_RECHECK
+
+
+def flops_per_sample_layer(model):
+    """Algorithmic FP32 work of the brute-force screen: per candidate d fused
+    multiply-adds (2d flops) and one comparison (Sec. 4 counts 6 operations per
+    2-d distance with 3 additions, 2 multiplications and 1 comparison)."""
+    N = np.asarray(model.N, dtype=np.float64)
+    cand = np.sum(N[:-1] + N[1:]) / model.n
+    return float(cand * (2 * model.d + 1))
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for d in ("paper_1101_3228_gb300/csrc", "include"):
+        for f in sorted(os.listdir(os.path.join(ROOT, d))):
+            if f.endswith((".cu", ".cuh", ".h")):
+                h.update(open(os.path.join(ROOT, d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sms.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sms:
+            return None
+        load = [s for s in sms if mx and s > 0.5 * mx] or sms
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def cpu_baseline(model, grids_np, seconds):
+    """The oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    prec = model.prec
+    Ms = 20000 if model.d <= 2 else 4000
+    # size the sample from one probe layer so that the run takes about `seconds`
+    t = time.perf_counter()
+    mdl = model.restrict(n=1, M=Ms)
+    oracle.transitions(mdl, grids_np[: int(model.N[0] + model.N[1])], Ms, model.seed, prec)
+    dt = time.perf_counter() - t
+    per_sl = dt / Ms
+    layers = max(1, min(model.n, int(seconds / max(per_sl * Ms, 1e-9))))
+    M = int(max(1000, min(model.M, seconds / max(per_sl * layers, 1e-12))))
+    mdl = model.restrict(n=layers, M=M)
+    off = model.offsets()
+    t = time.perf_counter()
+    oracle.transitions(mdl, grids_np[: off[layers + 1]], M, model.seed, prec)
+    el = time.perf_counter() - t
+    return {"value": layers * M / el, "unit": "sample*layers/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {layers} of {model.n} layers x {M} pairs per layer (FP64 brute force, {el:.1f} s)"}
+
+
+def run_reference(args, model, rank, world):
+    """Reference arm: the CPU oracle, timed as it stands on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    g = W.layer_grids(model, samples=20000, iters=5) if model.grid_kind == "kmeans" else W.layer_grids(model)
+    probe = cpu_baseline(model, g, 2.0)
+    rate = probe["value"]
+    # each step: a bounded sample of the workload sized to ~ a few seconds
+    budget = max(1.0, 90.0 / max(1, args.steps + args.warmup))
+    layers = max(1, min(model.n, 4))
+    M = int(max(1000, min(model.M, budget * rate / layers)))
+    mdl = model.restrict(n=layers, M=M)
+    off = model.offsets()
+    gg = g[: off[layers + 1]]
+    for _ in range(args.warmup):
+        oracle.transitions(mdl, gg, M, model.seed, model.prec)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.transitions(mdl, gg, M, model.seed, model.prec)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    value = layers * M / (ms / 1e3)
+    sample = f"first {layers} of {model.n} layers x {M} pairs per layer per step"
+    line = {"impl": "reference", "metric": "certified sample*layers/s (exact counts)", "value": value,
+            "unit": "sample*layers/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": model.name, "d": model.d, "n": model.n,
+                                            "N": int(model.N[-1]), "M": model.M},
+            "cpu_baseline": {"value": value, "unit": "sample*layers/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "sample*layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    model = workload(args.config, args.M)
+    if args.impl == "reference":
+        run_reference(args, model, rank, world)
+        return
+
+    import torch
+    from paper_1101_3228_gb300 import binding as B
+    from paper_1101_3228_gb300 import build as libbuild
+    if rank == 0:
+        libbuild.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.barrier()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = B.Context(local)
+    stream = torch.cuda.current_stream()
+    seed = model.seed + 7919 * rank          # independent replica per rank
+    grids = ctx.build_grids(model, grid_method(model), samples=max(20 * int(np.max(model.N)), 200000),
+                            iters=20, seed=W.GRID_SEED_BASE + W.CONFIG_INDEX[model.name])
+    form = {"auto": B.FORM_AUTO, "plain_f64": B.FORM_PLAIN_F64, "f32_recheck": B.FORM_F32_RECHECK}.get(
+        args.form, B.FORM_AUTO)
+    if form == B.FORM_AUTO:
+        form = default_form(model, B)
+    prec = model.prec
+    opts = B.options(form=form, prec=prec)
+    counts = torch.empty(int(np.sum(model.N[:-1] * model.N[1:])), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # larger than the 129 MB L2
+    units = model.n * model.M
+
+    def step(o):
+        ctx.transitions(model, grids, model.M, seed, o, counts=counts, want_stats=False, stream=stream)
+
+    def timed(o, K, W_):
+        for _ in range(W_):
+            step(o)
+        torch.cuda.synchronize()
+        st = ctx.status()[1]
+        rech = st.rechecks
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        total, kern = 0.0, []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for i in range(K):
+            flush.fill_(i & 0xFF)                 # evict L2 between steps (outside the events)
+            ev[i][0].record(stream)
+            step(o)
+            ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            kern.append(ctx.status()[1].ms)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        total = sum(ms)
+        return total / K, kern, rech
+
+    with ClockSampler(local) as clk:
+        ms_step, kern_ms, rech = timed(opts, args.steps, max(3, args.warmup))
+    clocks = clk.summary()
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * units / (ms_step / 1e3)
+
+    # plain GPU comparator (exact FP64 brute force for d <= 2)
+    plain = None
+    pform = plain_form(model, B)
+    if args.plain_steps > 0 and pform != form:
+        po = B.options(form=pform, prec=prec)
+        pms, _, _ = timed(po, args.plain_steps, 1)
+        plain = {"form": B.FORM_NAMES[pform], "value": world * units / (pms / 1e3), "ms_per_step": pms}
+
+    # end to end through the public API: host grids and payoff in, price out
+    gh = grids.cpu().numpy()
+    phi = W.payoff_values(model, gh)
+    gpin = torch.from_numpy(gh).pin_memory()
+    ppin = torch.from_numpy(phi).pin_memory()
+    e2e_ms = []
+    for i in range(max(1, min(args.steps, 5)) + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        price, _ = ctx.price(model, gpin.numpy(), model.M, seed, ppin.numpy(), opts, stream=stream)
+        if i > 0:
+            e2e_ms.append(1e3 * (time.perf_counter() - t))
+    e2e = {"value": world * units / (statistics.mean(e2e_ms) / 1e3), "unit": "sample*layers/s",
+           "h2d_bytes_per_step": int(gh.nbytes + phi.nbytes), "d2h_bytes_per_step": 8,
+           "ms_per_step": statistics.mean(e2e_ms), "price": price}
+
+    # roofline of the dominant kernel (the persistent forward kernel)
+    peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    kmean = statistics.mean(kern_ms) if kern_ms and all(k > 0 for k in kern_ms) else ms_step
+    flops = flops_per_sample_layer(model) * units / world
+    peak = 2.0 * FP32_LANES_PER_SM * n_sm * sm_max * 1e6 / 1e12
+    traffic = None
+    if os.path.exists(TRAFFIC):
+        tj = json.load(open(TRAFFIC))
+        ent = tj.get(model.name)
+        if ent and ent.get("source_hash") == source_hash() and ent.get("form") == B.FORM_NAMES[form]:
+            traffic = ent.get("bytes_per_launch")
+    achieved = flops / (kmean / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel_ms": kmean,
+                "peak_basis": f"FP32 FMA lanes: {n_sm} SMs x {FP32_LANES_PER_SM} x 2 flops x {sm_max:.0f} MHz"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(model, gh, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": "certified sample*layers/s (exact counts)", "value": value, "unit": "sample*layers/s",
+                "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": model.name, "d": model.d, "n": model.n, "N": int(model.N[-1]),
+                           "M": model.M, "form": B.FORM_NAMES[form],
+                           "sample_prec": "f32" if prec == 1 else "f64",
+                           "l2": "256 MiB buffer written between timed steps",
+                           "rechecks_per_step": rech},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+                "clocks": clocks, "plain": plain}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

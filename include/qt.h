@@ -1,0 +1,226 @@
+/*
+ * qt.h -- C ABI of libqt, the GB300 (sm_103a) library for the forward step of
+ * the Quantization Tree algorithm and its backward induction.
+ *
+ * Method: G. Pages and B. Wilbertz, "GPGPUs in computational finance: Massive
+ * parallel computing for American style options", arXiv:1101.3228.
+ *   Sec. 2        quantization grids Gamma_k, Voronoi cells, nearest-neighbour
+ *                 projection, transition probabilities (eq. (defPi)), the BDP
+ *                 recursion on the tree;
+ *   Sec. 3        the Gaussian 2-factor model, Prop. 1 (AR(1) form
+ *                 X_{k+1} = A_k X_k + T_k eps_k), Algorithm I;
+ *   Sec. 3.1-3.3  random numbers, nearest-neighbour search, counter updates;
+ *   Sec. 4        Algorithm III: every layer k draws M pairs (X_k, eps_k)
+ *                 independently, i = NN(X_k, Gamma_k),
+ *                 j = NN(A_k X_k + T_k eps_k, Gamma_{k+1}), counts p^k_ij,
+ *                 then pi^k_ij = p^k_ij / p^k_i.
+ *
+ * Conventions common to every entry point
+ *   - Status: every function returns a qt_status; 0 is success.  Errors never
+ *     unwind across the ABI.  qt_last_error() returns a message for the last
+ *     failing call on that context.
+ *   - Asynchrony: work is enqueued on the caller's CUDA stream (a cudaStream_t
+ *     passed as void*; NULL is the legacy default stream).  Functions that
+ *     return host results (qt_price, qt_get_status, and any call given a
+ *     non-NULL qt_stats*) synchronise that stream before returning.
+ *   - Ownership: every pointer argument is owned by the caller.  The library
+ *     owns only the context and the workspace it allocates inside it.  "dev"
+ *     marks device pointers, "host" marks host pointers; qt_price also accepts
+ *     host memory where it says so.
+ *   - Layout: all arrays are C-contiguous, row-major.  Grids of all layers are
+ *     concatenated: layer k occupies points [off_k, off_k + N_k) of a
+ *     [sum_k N_k][d] FP64 array.  Count matrices are concatenated the same way:
+ *     layer k is an [N_k][N_{k+1}] block at entry offset sum_{q<k} N_q N_{q+1}.
+ *   - Exactness contract: the cell of a point z in Gamma is
+ *     argmin_i D64(z, x_i), D64 = sum_l (z_l - x_il)^2 accumulated left to
+ *     right in IEEE binary64 with round-to-nearest and no fused multiply-add;
+ *     equal distances go to the lowest index.  Every search form returns this
+ *     cell for every sample ("certified"), whatever precision it screens in.
+ *   - Sampler: Philox4x32-10 (Salmon et al., SC'11) with key (seed_lo, seed_hi)
+ *     and counter (m_lo, m_hi, k, r) for sample m of layer k and call r;
+ *     Box-Muller normals from uniforms u = (2 floor(w/2^9) + 1) 2^-24 (FP32)
+ *     or from two words (FP64), with ln, sin and cos evaluated by fixed
+ *     series in correctly rounded arithmetic; z = normals [0,d),
+ *     eps = normals [d,2d); X_k = m_k + L_k z; Y = A_k X_k + b_k + T_k eps,
+ *     each product and sum rounded in order in the sample precision.  The
+ *     samples are therefore the same bits on any IEEE machine.
+ */
+#ifndef QT_H
+#define QT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QT_API __attribute__((visibility("default")))
+#else
+#define QT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t qt_status;
+#define QT_OK 0
+#define QT_EINVAL 1          /* an argument is out of range or inconsistent            */
+#define QT_ENOMEM 2          /* a device or host allocation failed                     */
+#define QT_ECUDA 3           /* a CUDA runtime call failed (message has the CUDA error) */
+#define QT_ETIMEOUT 4        /* a bounded device wait ran out; results are not valid    */
+#define QT_EUNSUPPORTED 5    /* the request needs a form or size this build lacks       */
+#define QT_EDEVICE 6         /* a kernel reported an internal inconsistency             */
+
+/* search forms (qt_options.form) */
+#define QT_FORM_AUTO 0        /* library picks the fastest certified form                */
+#define QT_FORM_PLAIN_F64 1   /* brute force, exact FP64 distances                       */
+#define QT_FORM_F32_RECHECK 2 /* FP32 brute-force screen, FP64 recheck of near ties      */
+#define QT_FORM_TC_RECHECK 3  /* tensor-core (tcgen05) screen, FP64 recheck              */
+#define QT_FORM_ROUTER_CERT 4 /* learned start cell + Elkan certificate, brute fallback  */
+
+/* sample precision (qt_options.sample_prec) */
+#define QT_PREC_F64 0
+#define QT_PREC_F32 1
+
+/* count element type (qt_options.counts_type) */
+#define QT_COUNTS_I64 0
+#define QT_COUNTS_U32 1
+
+/* qt_options.flags */
+#define QT_FLAG_NO_GRAPH 1u   /* launch kernels directly instead of replaying a CUDA graph */
+#define QT_FLAG_NO_TUNE 2u    /* skip the autotuner, use the built-in tile choice            */
+#define QT_FLAG_SMEM_HIST 4u  /* force the shared-memory privatised histogram                */
+#define QT_FLAG_GLOBAL_HIST 8u /* force direct L2 atomics for the counts                     */
+
+/* grid-building methods (qt_build_grids) */
+#define QT_GRID_LLOYD1D 1     /* d = 1: stationary quantizer of N(0,1) (Newton on Lloyd's map) */
+#define QT_GRID_PRODUCT 2     /* product of 1-d stationary quantizers                          */
+#define QT_GRID_KMEANS 3      /* sample Lloyd (k-means) on seeded N(0, I_d) draws              */
+
+typedef struct qt_ctx qt_ctx;
+
+/* The Markov chain of Prop. 1 on layers k = 0..n (host arrays, FP64).
+ *   N [n+1]        grid sizes N_k >= 1 (N_0 = 1 when X_0 is deterministic)
+ *   A [n][d][d]    AR(1) matrices A_k
+ *   b [n][d]       drifts b_k (zero for the OU model of Sec. 3)
+ *   T [n][d][d]    innovation factors T_k, read as lower triangular
+ *   m [n+1][d]     mean of X_k
+ *   L [n+1][d][d]  lower-triangular factor of Cov(X_k), read as lower triangular
+ * 1 <= d <= 16, 1 <= n <= 65535.                                                 */
+typedef struct {
+    int32_t d;
+    int32_t n;
+    const int64_t* N;
+    const double* A;
+    const double* b;
+    const double* T;
+    const double* m;
+    const double* L;
+} qt_model;
+
+typedef struct {
+    int32_t form;          /* QT_FORM_*                                                    */
+    int32_t sample_prec;   /* QT_PREC_*                                                    */
+    int32_t counts_type;   /* QT_COUNTS_* (element type of the counts array)               */
+    uint32_t flags;        /* QT_FLAG_*                                                    */
+    int64_t spin_budget;   /* iterations of every bounded device wait; 0 = library default;
+                              negative = give up at once (tests of the timeout path)       */
+    const void* router;    /* qt_router* for QT_FORM_ROUTER_CERT, else NULL                */
+    int32_t tile_samples_per_thread; /* 0 = autotuned                                       */
+    int32_t reserved[3];
+} qt_options;
+
+/* Optional per-sample record: sample t of layer k is m = t * stride, t < count.
+ * X, Y: dev FP64 [n][count][d]; i, j: dev int32 [n][count] (-1 where m >= M). */
+typedef struct {
+    int64_t count;
+    int64_t stride;
+    double* X;
+    double* Y;
+    int32_t* i;
+    int32_t* j;
+} qt_dump;
+
+/* Filled by calls given a non-NULL qt_stats* (the call then synchronises). */
+typedef struct {
+    int64_t samples;        /* sample pairs processed (n * M)                        */
+    int64_t rechecks;       /* FP64 re-evaluations of an uncertain screened search   */
+    int64_t searches;       /* nearest-cell searches (2 per sample pair)              */
+    int64_t candidates;     /* screened candidate distances (router form)             */
+    int32_t form_used;      /* QT_FORM_* actually run                                 */
+    int32_t device_status;  /* qt_status reported by the kernels                      */
+    double ms;              /* device time of the forward step, if measured, else 0   */
+} qt_stats;
+
+/* Context: one per device.  device = CUDA ordinal.  Not thread safe; use one
+ * context per host thread.  qt_destroy frees everything the context owns.    */
+QT_API qt_status qt_create(qt_ctx** ctx, int32_t device);
+QT_API qt_status qt_destroy(qt_ctx* ctx);
+QT_API const char* qt_last_error(const qt_ctx* ctx);
+QT_API const char* qt_status_string(qt_status s);
+/* Default options: AUTO form, FP32 samples, int64 counts, autotuned tiles. */
+QT_API void qt_default_options(qt_options* opts);
+
+/* Grids for every layer (Sec. 2: grids that minimise the quadratic error of
+ * eq. (Qerr); the paper's precomputed optimal Gaussian grids are replaced by
+ * stationary quantizers built here).  Layer k gets m_k + L_k g for a base grid
+ * g of N(0, I_d) with N_k points.  method = QT_GRID_*; samples and iters are
+ * used by QT_GRID_KMEANS (training draws, Lloyd iterations); tol is the Newton
+ * tolerance of the 1-d quantizer.  grids: dev FP64 [sum_k N_k][d], written.   */
+QT_API qt_status qt_build_grids(qt_ctx* ctx, const qt_model* model, int32_t method, int64_t samples,
+                         int32_t iters, double tol, uint64_t seed, double* grids, void* stream);
+
+/* Algorithm III (Sec. 4): for k = 0..n-1 and m = 0..M-1 draw (X_k, eps_k),
+ * find i = NN(X_k, Gamma_k) and j = NN(A_k X_k + b_k + T_k eps_k, Gamma_{k+1})
+ * and add 1 to p^k_ij.  All layers run in one persistent launch.
+ *   grids  dev FP64 [sum_k N_k][d]
+ *   counts dev [sum_k N_k N_{k+1}] of opts->counts_type, OVERWRITTEN (zeroed
+ *          first); p^k_i = sum_j p^k_ij is not stored (row sums).
+ *   M      samples per layer, 1 <= M < 2^32
+ *   dump   optional per-sample record (may be NULL); stats optional.        */
+QT_API qt_status qt_transitions(qt_ctx* ctx, const qt_model* model, const double* grids, int64_t M,
+                         uint64_t seed, const qt_options* opts, void* counts, const qt_dump* dump,
+                         qt_stats* stats, void* stream);
+
+/* Counting step of Algorithm III on caller-supplied samples (one layer pair):
+ * counts[NA][NB] (dev, opts->counts_type) is OVERWRITTEN with
+ * #{t : NN(X_t, gA) = i, NN(Y_t, gB) = j}.  gA dev FP64 [NA][d], gB [NB][d],
+ * X, Y dev FP64 [M][d] (finite values).  ii/jj (dev int32 [M]) receive the
+ * cells when non-NULL.                                                         */
+QT_API qt_status qt_counts_from_samples(qt_ctx* ctx, int32_t d, const double* gA, int64_t NA,
+                                 const double* gB, int64_t NB, const double* X, const double* Y,
+                                 int64_t M, const qt_options* opts, void* counts, int32_t* ii,
+                                 int32_t* jj, qt_stats* stats, void* stream);
+
+/* BDP recursion on the tree (Sec. 2): V_n = phi_n and, for k = n-1..0,
+ * V_k(i) = max(phi_k(i), sum_j pi^k_ij V_{k+1}(j)) with pi^k_ij = p^k_ij / p^k_i
+ * (Algorithm III's normalisation).  A row with p^k_i = 0 has no continuation:
+ * V_k(i) = phi_k(i).  The continuation is evaluated as
+ * (sum_j p^k_ij V_{k+1}(j)) / p^k_i in FP64, j summed in lanes j mod 32 and
+ * combined by a fixed butterfly, so results are bitwise reproducible.
+ *   N      host int64 [n+1]
+ *   counts dev, counts_type elements, concatenated as in qt_transitions
+ *   phi, V dev FP64 [sum_k N_k] (V written)                                    */
+QT_API qt_status qt_backward(qt_ctx* ctx, int32_t n, const int64_t* N, const void* counts,
+                      int32_t counts_type, const double* phi, double* V, void* stream);
+
+/* Forward step + backward induction + root value: the option price V^_0.
+ * If N_0 = 1 the price is V_0(0); otherwise sum_i (p^0_i / M) V_0(i).
+ * grids and phi may be host or dev pointers (FP64 [sum_k N_k][d] and
+ * [sum_k N_k]); price is a host double.  Synchronises the stream.             */
+QT_API qt_status qt_price(qt_ctx* ctx, const qt_model* model, const double* grids, int64_t M,
+                   uint64_t seed, const qt_options* opts, const double* phi, double* price,
+                   qt_stats* stats, void* stream);
+
+/* Synchronise the stream and return the device status of the last forward
+ * call on this context (QT_OK, QT_ETIMEOUT or QT_EDEVICE).                    */
+QT_API qt_status qt_get_status(qt_ctx* ctx, void* stream, qt_stats* stats);
+
+/* Device bytes the context will allocate for a qt_transitions call of this
+ * shape (descriptor tables, prepared grids, status words).                   */
+QT_API qt_status qt_transitions_workspace(const qt_model* model, const qt_options* opts, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QT_H */

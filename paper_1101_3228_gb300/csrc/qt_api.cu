@@ -1,0 +1,1003 @@
+// qt_api.cu -- host side of libqt: contexts, workspace, descriptor tables,
+// CUDA-graph capture of the forward step, the autotuner, and every C-ABI entry
+// point declared in include/qt.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <string>
+#include <vector>
+
+#include "../../include/qt.h"
+#include "qt_internal.h"
+#include "qt_launch.h"
+
+namespace qt {
+__global__ void prep_records_kernel(const double*, GridInfo*, int, int, int, int, long long, float*, double*);
+__global__ void backward_layer_kernel(const void*, int, long long, int, int, const double*, const double*, double*);
+__global__ void root_price_kernel(const void*, int, int, int, const double*, double*);
+__global__ void kmeans_draw_kernel(int, unsigned long long, long long, float*);
+__global__ void kmeans_assign_kernel(int, long long, const float*, int, const float*, unsigned long long*,
+                                     unsigned long long*, int);
+__global__ void kmeans_update_kernel(int, int, const unsigned long long*, const unsigned long long*, float*);
+__global__ void map_grid_kernel(int, int, const double*, const double*, const double*, double*);
+}  // namespace qt
+
+using namespace qt;
+
+// ------------------------------------------------------------------ context
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct HostBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct TuneKey {
+    int form, dm, prec, nbucket;
+    bool operator<(const TuneKey& o) const
+    {
+        return std::tie(form, dm, prec, nbucket) < std::tie(o.form, o.dm, o.prec, o.nbucket);
+    }
+};
+
+}  // namespace
+
+struct qt_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    std::string err;
+    std::map<std::string, DevBuf> dev;
+    std::map<std::string, HostBuf> host;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev_tables = nullptr;   // last use of the pinned descriptor tables
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;   // around the forward kernel (stats.ms)
+    bool timed = false;
+    // cached graph of the last forward call
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> gkey;
+    // autotuner cache: key -> samples per thread
+    std::map<TuneKey, int> tune;
+    int last_form = 0;
+};
+
+namespace {
+
+qt_status fail(qt_ctx* c, qt_status s, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define QT_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? QT_ENOMEM : QT_ECUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                        \
+        }                                                                                      \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+// Host-side fault injection for the allocation-failure tests: QT_FAULT=alloc
+// makes the next workspace allocation fail as if the device were out of memory.
+bool injected_alloc_failure()
+{
+    const char* f = getenv("QT_FAULT");
+    return f && strcmp(f, "alloc") == 0;
+}
+
+qt_status dev_get(qt_ctx* ctx, const char* name, size_t bytes, void** out)
+{
+    DevBuf& b = ctx->dev[name];
+    if (b.bytes < bytes) {
+        if (injected_alloc_failure()) return fail(ctx, QT_ENOMEM, "workspace '%s': injected allocation failure", name);
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        size_t want = std::max<size_t>(bytes, 256);
+        cudaError_t e = cudaMalloc(&b.p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return fail(ctx, QT_ENOMEM, "workspace '%s' (%zu bytes): %s", name, want, cudaGetErrorString(e));
+        }
+        b.bytes = want;
+        // a workspace that moved invalidates the cached graph
+        if (ctx->gexec) {
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+            ctx->gkey.clear();
+        }
+    }
+    *out = b.p;
+    return QT_OK;
+}
+
+qt_status host_get(qt_ctx* ctx, const char* name, size_t bytes, void** out)
+{
+    HostBuf& b = ctx->host[name];
+    if (b.bytes < bytes) {
+        if (ctx->ev_tables) cudaEventSynchronize(ctx->ev_tables);
+        if (b.p) cudaFreeHost(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        size_t want = std::max<size_t>(bytes, 256);
+        cudaError_t e = cudaMallocHost(&b.p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, QT_ENOMEM, "pinned host buffer '%s': %s", name, cudaGetErrorString(e));
+        }
+        b.bytes = want;
+        if (ctx->gexec) {
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+            ctx->gkey.clear();
+        }
+    }
+    *out = b.p;
+    return QT_OK;
+}
+
+qt_status validate_model(qt_ctx* ctx, const qt_model* m)
+{
+    if (!m) return fail(ctx, QT_EINVAL, "model is NULL");
+    if (m->d < 1 || m->d > kDMax) return fail(ctx, QT_EINVAL, "d = %d outside [1, %d]", m->d, kDMax);
+    if (m->n < 1 || m->n > 65535) return fail(ctx, QT_EINVAL, "n = %d outside [1, 65535]", m->n);
+    if (!m->N || !m->A || !m->b || !m->T || !m->m || !m->L) return fail(ctx, QT_EINVAL, "model array is NULL");
+    for (int k = 0; k <= m->n; ++k)
+        if (m->N[k] < 1 || m->N[k] > (1 << 24)) return fail(ctx, QT_EINVAL, "N[%d] = %lld outside [1, 2^24]", k, (long long)m->N[k]);
+    return QT_OK;
+}
+
+int dm_for(int d)
+{
+    static const int dms[] = {1, 2, 3, 4, 6, 8, 10, 12, 16};
+    for (int v : dms)
+        if (v >= d) return v;
+    return 0;
+}
+
+int rec_floats_for(int dm) { return 4 * ((dm + 1 + 3) / 4); }
+int rec64_for(int dm) { return (dm + 1) / 2 * 2; }
+long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ public: context
+
+extern "C" qt_status qt_create(qt_ctx** out, int32_t device)
+{
+    qt_ctx* ctx = nullptr;
+    if (!out) return QT_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return QT_ECUDA;
+    }
+    if (device < 0 || device >= ndev) return QT_EINVAL;
+    ctx = new (std::nothrow) qt_ctx();
+    if (!ctx) return QT_ENOMEM;
+    ctx->device = device;
+    DeviceGuard g(device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete ctx;
+        return QT_ECUDA;
+    }
+    if (prop.major * 10 + prop.minor < 100) {
+        delete ctx;
+        return QT_EUNSUPPORTED;
+    }
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_tables, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev_k0) != cudaSuccess || cudaEventCreate(&ctx->ev_k1) != cudaSuccess) {
+        delete ctx;
+        return QT_ECUDA;
+    }
+    *out = ctx;
+    return QT_OK;
+}
+
+extern "C" qt_status qt_destroy(qt_ctx* ctx)
+{
+    if (!ctx) return QT_OK;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    for (auto& kv : ctx->dev)
+        if (kv.second.p) cudaFree(kv.second.p);
+    for (auto& kv : ctx->host)
+        if (kv.second.p) cudaFreeHost(kv.second.p);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->ev_tables) cudaEventDestroy(ctx->ev_tables);
+    if (ctx->ev_k0) cudaEventDestroy(ctx->ev_k0);
+    if (ctx->ev_k1) cudaEventDestroy(ctx->ev_k1);
+    delete ctx;
+    return QT_OK;
+}
+
+extern "C" const char* qt_last_error(const qt_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+extern "C" const char* qt_status_string(qt_status s)
+{
+    switch (s) {
+    case QT_OK: return "ok";
+    case QT_EINVAL: return "invalid argument";
+    case QT_ENOMEM: return "out of memory";
+    case QT_ECUDA: return "CUDA error";
+    case QT_ETIMEOUT: return "device wait timed out";
+    case QT_EUNSUPPORTED: return "unsupported";
+    case QT_EDEVICE: return "device-side error";
+    default: return "unknown status";
+    }
+}
+
+extern "C" void qt_default_options(qt_options* o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->form = QT_FORM_AUTO;
+    o->sample_prec = QT_PREC_F32;
+    o->counts_type = QT_COUNTS_I64;
+}
+
+// ------------------------------------------------------------------ forward step
+
+namespace {
+
+struct Plan {
+    int form = 0, dm = 0, S = 0, block = 256;
+    int d = 0, n = 0, ngrids = 0;
+    long long total_recs = 0;
+    size_t grid_bytes = 0, hist_bytes = 0, dyn_smem = 0;
+    long long total_items = 0;
+    int tile = 0;
+    int rec_floats = 0, rec64 = 0, pstride = 0;
+    std::vector<LayerDesc> layers;
+    std::vector<GridInfo> grids;
+    long long count_entries = 0;
+};
+
+struct FwdIO {
+    const double* g64;           // concatenated FP64 grids (caller's or workspace copy)
+    const float* params_f_host;  // not used directly
+    void* counts;
+    const qt_dump* dump;
+    const double* srcX;
+    const double* srcY;
+    int32_t* cellsA;
+    int32_t* cellsB;
+};
+
+// Pick form, dimension class, tile and shared memory for a problem described
+// by grid sizes Ns (n+1 entries) and centres mus ((n+1) x d).
+qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, long long M, const qt_options* o,
+                    bool from_arrays, Plan& P)
+{
+    P.d = d;
+    P.n = n;
+    P.dm = dm_for(d);
+    int form = o->form;
+    if (form == QT_FORM_AUTO) form = QT_FORM_F32_RECHECK;
+    if (form == QT_FORM_TC_RECHECK || form == QT_FORM_ROUTER_CERT)
+        return fail(ctx, QT_EUNSUPPORTED, "search form %d is not available in this build", form);
+    if (form != QT_FORM_PLAIN_F64 && form != QT_FORM_F32_RECHECK)
+        return fail(ctx, QT_EINVAL, "unknown search form %d", form);
+    P.form = form == QT_FORM_PLAIN_F64 ? kPlainF64 : kF32Recheck;
+    if (!from_arrays && o->sample_prec != QT_PREC_F32 && o->sample_prec != QT_PREC_F64)
+        return fail(ctx, QT_EINVAL, "sample_prec %d", o->sample_prec);
+    P.rec_floats = rec_floats_for(P.dm);
+    P.rec64 = rec64_for(P.dm);
+    P.pstride = (int)round_up(2 * d + 3 * d * d, 4);
+    P.ngrids = n + 1;
+    P.grids.resize(P.ngrids);
+    long long goff = 0, roff = 0;
+    for (int g = 0; g < P.ngrids; ++g) {
+        GridInfo& G = P.grids[g];
+        memset(&G, 0, sizeof G);
+        for (int l = 0; l < d; ++l) G.mu[l] = (float)mus[(long long)g * d + l];
+        G.R = 0.0f;
+        G.N = (int)Ns[g];
+        G.Npad = P.form == kF32Recheck ? (int)round_up(Ns[g], kChunk) : (int)Ns[g];
+        G.goff = goff;
+        G.roff = roff;
+        goff += Ns[g];
+        roff += G.Npad;
+    }
+    P.total_recs = roff;
+    const size_t rec_bytes = P.form == kF32Recheck ? (size_t)P.rec_floats * 4 : (size_t)P.rec64 * 8;
+    // samples per thread: tuned value if present, else a register-budget heuristic
+    int S = o->tile_samples_per_thread;
+    if (S <= 0) {
+        TuneKey key{P.form, P.dm, from_arrays ? 0 : o->sample_prec, 0};
+        auto it = ctx->tune.find(key);
+        S = it != ctx->tune.end() ? it->second : (P.form == kPlainF64 ? 2 : (P.dm <= 2 ? 8 : (P.dm <= 4 ? 4 : 2)));
+    }
+    if (!forward_variant_exists(P.form, P.dm, S))
+        return fail(ctx, QT_EUNSUPPORTED, "no kernel for form %d, d %d, %d samples per thread", form, d, S);
+    P.S = S;
+    P.block = 256;
+    P.tile = P.block * S;
+    // shared memory: both grids resident; the private histogram when it fits
+    size_t budget = ctx->smem_optin > 24 * 1024 ? ctx->smem_optin - 24 * 1024 : 0;
+    size_t gmax = 0;
+    for (int k = 0; k < n; ++k) {
+        const size_t b = (size_t)(P.grids[k].Npad + P.grids[k + 1].Npad) * rec_bytes;
+        gmax = std::max(gmax, b);
+    }
+    if (gmax > budget)
+        return fail(ctx, QT_EUNSUPPORTED,
+                    "grids of %zu bytes per layer pair exceed the %zu bytes of shared memory of the resident mode",
+                    gmax, budget);
+    P.grid_bytes = round_up((long long)gmax, 128);
+    const bool force_smem = (o->flags & QT_FLAG_SMEM_HIST) != 0;
+    const bool force_glob = (o->flags & QT_FLAG_GLOBAL_HIST) != 0;
+    size_t hmax = 0;
+    P.layers.resize(n);
+    long long item = 0, coff = 0;
+    const long long items_per_layer = (M + P.tile - 1) / P.tile;
+    for (int k = 0; k < n; ++k) {
+        LayerDesc& L = P.layers[k];
+        memset(&L, 0, sizeof L);
+        L.NA = (int)Ns[k];
+        L.NB = (int)Ns[k + 1];
+        L.NApad = P.grids[k].Npad;
+        L.NBpad = P.grids[k + 1].Npad;
+        L.gridA = k;
+        L.gridB = k + 1;
+        L.goffA = P.grids[k].goff;
+        L.goffB = P.grids[k + 1].goff;
+        L.roffA = P.grids[k].roff;
+        L.roffB = P.grids[k + 1].roff;
+        L.coff = coff;
+        L.item_begin = item;
+        L.items = (int)items_per_layer;
+        const size_t hb = (size_t)L.NA * L.NB * 4;
+        // privatise when the histogram fits and each CTA sees enough samples of
+        // the layer to amortise the flush (or when forced)
+        const long long ctas = (long long)ctx->num_sms * 2;
+        const bool dense_enough = (M / std::max<long long>(ctas, 1)) >= 2 * (long long)L.NA * L.NB;
+        L.hist_smem = !force_glob && hb + P.grid_bytes <= budget && (force_smem || dense_enough);
+        if (L.hist_smem) hmax = std::max(hmax, hb);
+        item += items_per_layer;
+        coff += (long long)L.NA * L.NB;
+    }
+    P.total_items = item;
+    P.count_entries = coff;
+    P.hist_bytes = round_up((long long)hmax, 16);
+    P.dyn_smem = P.grid_bytes + P.hist_bytes;
+    return QT_OK;
+}
+
+// Enqueue the whole forward step on `st`: table uploads, zeroing, record
+// preparation, the persistent kernel.
+qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long M, unsigned long long seed,
+                          const qt_options* o, int source, void* dparams_f, void* dparams_d, const void* hparams_f,
+                          const void* hparams_d, size_t pcount, void* dlayers, void* dgrids, const void* hlayers,
+                          const void* hgrids, void* drec32, void* drec64, DevStatus* dstatus, cudaStream_t st)
+{
+    QT_CUDA(cudaMemcpyAsync(dparams_f, hparams_f, pcount * 4, cudaMemcpyHostToDevice, st));
+    QT_CUDA(cudaMemcpyAsync(dparams_d, hparams_d, pcount * 8, cudaMemcpyHostToDevice, st));
+    QT_CUDA(cudaMemcpyAsync(dlayers, hlayers, sizeof(LayerDesc) * P.layers.size(), cudaMemcpyHostToDevice, st));
+    QT_CUDA(cudaMemcpyAsync(dgrids, hgrids, sizeof(GridInfo) * P.grids.size(), cudaMemcpyHostToDevice, st));
+    QT_CUDA(cudaMemsetAsync(dstatus, 0, sizeof(DevStatus), st));
+    const size_t csize = o->counts_type == QT_COUNTS_U32 ? 4 : 8;
+    QT_CUDA(cudaMemsetAsync(io.counts, 0, csize * (size_t)P.count_entries, st));
+    if (io.dump && io.dump->count > 0) {
+        QT_CUDA(cudaMemsetAsync(io.dump->i, 0xFF, sizeof(int32_t) * (size_t)io.dump->count * P.n, st));
+        QT_CUDA(cudaMemsetAsync(io.dump->j, 0xFF, sizeof(int32_t) * (size_t)io.dump->count * P.n, st));
+    }
+    {
+        const int blk = 256;
+        const long long nb = (P.total_recs + blk - 1) / blk;
+        prep_records_kernel<<<(unsigned)nb, blk, 0, st>>>(
+            io.g64, (GridInfo*)dgrids, P.ngrids, P.d, P.rec_floats, P.rec64, P.total_recs,
+            P.form == kF32Recheck ? (float*)drec32 : nullptr, P.form == kPlainF64 ? (double*)drec64 : nullptr);
+        QT_CUDA(cudaGetLastError());
+    }
+    ForwardParams fp;
+    memset(&fp, 0, sizeof fp);
+    fp.d = P.d;
+    fp.n = P.n;
+    fp.form = P.form;
+    fp.source = source;
+    fp.prec = o->sample_prec == QT_PREC_F32 ? 1 : 0;
+    fp.counts_u32 = o->counts_type == QT_COUNTS_U32;
+    fp.M = (unsigned long long)M;
+    fp.seed = seed;
+    fp.total_items = P.total_items;
+    fp.tile = P.tile;
+    fp.rec_floats = P.rec_floats;
+    fp.rec64_doubles = P.rec64;
+    fp.smem_grid_bytes = (int)P.grid_bytes;
+    fp.smem_hist_entries = (int)(P.hist_bytes / 4);
+    fp.spin_budget = o->spin_budget == 0 ? (1ll << 26) : o->spin_budget;
+    fp.layers = (const LayerDesc*)dlayers;
+    fp.grids = (const GridInfo*)dgrids;
+    fp.params_f = (const float*)dparams_f;
+    fp.params_d = (const double*)dparams_d;
+    fp.params_stride = P.pstride;
+    fp.g64 = io.g64;
+    fp.rec32 = (const float*)drec32;
+    fp.rec64 = (const double*)drec64;
+    fp.srcX = io.srcX;
+    fp.srcY = io.srcY;
+    fp.counts = io.counts;
+    fp.cellsA = io.cellsA;
+    fp.cellsB = io.cellsB;
+    if (io.dump && io.dump->count > 0) {
+        fp.dump_count = io.dump->count;
+        fp.dump_stride = io.dump->stride;
+        fp.dumpX = io.dump->X;
+        fp.dumpY = io.dump->Y;
+        fp.dumpI = io.dump->i;
+        fp.dumpJ = io.dump->j;
+    }
+    fp.status = dstatus;
+    int blocks_per_sm = 0;
+    QT_CUDA(cudaEventRecord(ctx->ev_k0, st));
+    cudaError_t e = forward_launch(P.form, P.dm, P.S, fp, P.block, (int)P.dyn_smem, ctx->num_sms, &blocks_per_sm, st);
+    if (e != cudaSuccess) return fail(ctx, QT_ECUDA, "forward kernel launch: %s", cudaGetErrorString(e));
+    QT_CUDA(cudaEventRecord(ctx->ev_k1, st));
+    ctx->timed = true;
+    return QT_OK;
+}
+
+qt_status read_status(qt_ctx* ctx, cudaStream_t st, qt_stats* stats, long long samples, long long searches)
+{
+    void* dstatus = ctx->dev["status"].p;
+    DevStatus hs;
+    memset(&hs, 0, sizeof hs);
+    QT_CUDA(cudaStreamSynchronize(st));
+    if (dstatus) QT_CUDA(cudaMemcpy(&hs, dstatus, sizeof hs, cudaMemcpyDeviceToHost));
+    if (stats) {
+        stats->samples = samples;
+        stats->searches = searches;
+        stats->rechecks = (int64_t)hs.rechecks;
+        stats->candidates = (int64_t)hs.candidates;
+        stats->form_used = ctx->last_form;
+        stats->device_status = hs.code;
+        stats->ms = 0.0;
+        float ms = 0.f;
+        if (ctx->timed && cudaEventElapsedTime(&ms, ctx->ev_k0, ctx->ev_k1) == cudaSuccess) stats->ms = ms;
+        cudaGetLastError();
+    }
+    if (hs.code == QT_ETIMEOUT) return fail(ctx, QT_ETIMEOUT, "a bounded device wait ran out (site %d)", hs.where);
+    if (hs.code != 0) return fail(ctx, QT_EDEVICE, "kernel reported status %d at site %d", hs.code, hs.where);
+    return QT_OK;
+}
+
+bool stream_is_capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+void key_append(std::vector<unsigned char>& k, const void* p, size_t n)
+{
+    const unsigned char* b = (const unsigned char*)p;
+    k.insert(k.end(), b, b + n);
+}
+
+// Shared body of qt_transitions and qt_counts_from_samples.
+qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, const double* params_d_host,
+                         long long M, unsigned long long seed, const qt_options* o, int source, const FwdIO& io,
+                         qt_stats* stats, cudaStream_t st)
+{
+    Plan P;
+    qt_status s = make_plan(ctx, d, n, Ns, mus, M, o, source == kArrays, P);
+    if (s) return s;
+    ctx->last_form = P.form == kPlainF64 ? QT_FORM_PLAIN_F64 : QT_FORM_F32_RECHECK;
+    // device workspace
+    void *dlayers, *dgrids, *dpf, *dpd, *drec32 = nullptr, *drec64 = nullptr, *dstatus;
+    const size_t pbytes = (size_t)std::max(1, n) * P.pstride;
+    if ((s = dev_get(ctx, "layers", sizeof(LayerDesc) * P.layers.size(), &dlayers))) return s;
+    if ((s = dev_get(ctx, "grids", sizeof(GridInfo) * P.grids.size(), &dgrids))) return s;
+    if ((s = dev_get(ctx, "params_f", pbytes * 4, &dpf))) return s;
+    if ((s = dev_get(ctx, "params_d", pbytes * 8, &dpd))) return s;
+    if (P.form == kF32Recheck) {
+        if ((s = dev_get(ctx, "rec32", (size_t)P.total_recs * P.rec_floats * 4, &drec32))) return s;
+    } else {
+        if ((s = dev_get(ctx, "rec64", (size_t)P.total_recs * P.rec64 * 8, &drec64))) return s;
+    }
+    if ((s = dev_get(ctx, "status", sizeof(DevStatus), &dstatus))) return s;
+    // pinned host tables (kept alive for graph replays)
+    void *hlayers, *hgrids, *hpf, *hpd;
+    if ((s = host_get(ctx, "layers", sizeof(LayerDesc) * P.layers.size(), &hlayers))) return s;
+    if ((s = host_get(ctx, "grids", sizeof(GridInfo) * P.grids.size(), &hgrids))) return s;
+    if ((s = host_get(ctx, "params_f", pbytes * 4, &hpf))) return s;
+    if ((s = host_get(ctx, "params_d", pbytes * 8, &hpd))) return s;
+    // the previous replay may still read the pinned tables
+    QT_CUDA(cudaEventSynchronize(ctx->ev_tables));
+    memcpy(hlayers, P.layers.data(), sizeof(LayerDesc) * P.layers.size());
+    memcpy(hgrids, P.grids.data(), sizeof(GridInfo) * P.grids.size());
+    float* pf = (float*)hpf;
+    double* pd = (double*)hpd;
+    memset(pf, 0, pbytes * 4);
+    memset(pd, 0, pbytes * 8);
+    if (params_d_host) {
+        for (long long e = 0; e < (long long)n * P.pstride; ++e) {
+            pd[e] = params_d_host[e];
+            pf[e] = (float)params_d_host[e];
+        }
+    }
+    // graph key: everything the enqueued work depends on
+    std::vector<unsigned char> key;
+    key_append(key, &P.form, sizeof P.form);
+    key_append(key, &P.S, sizeof P.S);
+    key_append(key, &M, sizeof M);
+    key_append(key, &seed, sizeof seed);
+    key_append(key, &source, sizeof source);
+    key_append(key, o, sizeof *o);
+    key_append(key, &io, sizeof io);
+    if (io.dump) key_append(key, io.dump, sizeof *io.dump);
+    key_append(key, P.layers.data(), sizeof(LayerDesc) * P.layers.size());
+    key_append(key, P.grids.data(), sizeof(GridInfo) * P.grids.size());
+    key_append(key, pd, pbytes * 8);
+
+    const bool direct = (o->flags & QT_FLAG_NO_GRAPH) || stream_is_capturing(st);
+    if (direct) {
+        s = enqueue_forward(ctx, P, io, M, seed, o, source, dpf, dpd, hpf, hpd, pbytes, dlayers, dgrids, hlayers,
+                            hgrids, drec32, drec64, (DevStatus*)dstatus, st);
+        if (s) return s;
+    } else {
+        if (!ctx->gexec || key != ctx->gkey) {
+            if (ctx->gexec) {
+                cudaGraphExecDestroy(ctx->gexec);
+                ctx->gexec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            QT_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t ce = cudaSuccess;
+            qt_status es = enqueue_forward(ctx, P, io, M, seed, o, source, dpf, dpd, hpf, hpd, pbytes, dlayers,
+                                           dgrids, hlayers, hgrids, drec32, drec64, (DevStatus*)dstatus,
+                                           ctx->cap_stream);
+            cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
+            if (es != QT_OK || ce != cudaSuccess || ee != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                if (es != QT_OK) return es;
+                return fail(ctx, QT_ECUDA, "graph capture: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+            }
+            cudaError_t ie = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                ctx->gexec = nullptr;
+                return fail(ctx, QT_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+            }
+            ctx->gkey = key;
+        }
+        QT_CUDA(cudaGraphLaunch(ctx->gexec, st));
+    }
+    QT_CUDA(cudaEventRecord(ctx->ev_tables, st));
+    if (stats) return read_status(ctx, st, stats, (long long)n * M, 2ll * n * M);
+    return QT_OK;
+}
+
+// Pack m, b, L, A, T of layer k (FP64) in the order the sampler reads them.
+void pack_params(const qt_model* m, int k, int pstride, double* out)
+{
+    const int d = m->d;
+    double* p = out + (long long)k * pstride;
+    for (int l = 0; l < d; ++l) p[l] = m->m[(long long)k * d + l];
+    for (int l = 0; l < d; ++l) p[d + l] = m->b[(long long)k * d + l];
+    for (int e = 0; e < d * d; ++e) {
+        const int r = e / d, c = e % d;
+        p[2 * d + e] = c <= r ? m->L[(long long)k * d * d + e] : 0.0;
+        p[2 * d + d * d + e] = m->A[(long long)k * d * d + e];
+        p[2 * d + 2 * d * d + e] = c <= r ? m->T[(long long)k * d * d + e] : 0.0;
+    }
+}
+
+}  // namespace
+
+extern "C" qt_status qt_transitions(qt_ctx* ctx, const qt_model* model, const double* grids, int64_t M, uint64_t seed,
+                                    const qt_options* opts, void* counts, const qt_dump* dump, qt_stats* stats,
+                                    void* stream)
+{
+    if (!ctx) return QT_EINVAL;
+    qt_status s = validate_model(ctx, model);
+    if (s) return s;
+    if (!grids || !counts) return fail(ctx, QT_EINVAL, "grids or counts is NULL");
+    if (M < 1 || M > 0xFFFFFFFFll) return fail(ctx, QT_EINVAL, "M = %lld outside [1, 2^32)", (long long)M);
+    qt_options o;
+    if (opts) o = *opts; else qt_default_options(&o);
+    if (o.counts_type != QT_COUNTS_I64 && o.counts_type != QT_COUNTS_U32)
+        return fail(ctx, QT_EINVAL, "counts_type %d", o.counts_type);
+    if (dump && dump->count > 0) {
+        if (dump->stride < 1 || !dump->X || !dump->Y || !dump->i || !dump->j)
+            return fail(ctx, QT_EINVAL, "dump needs stride >= 1 and four buffers");
+    }
+    DeviceGuard g(ctx->device);
+    const int d = model->d, n = model->n;
+    const int pstride = (int)round_up(2 * d + 3 * d * d, 4);
+    std::vector<double> params((size_t)n * pstride, 0.0);
+    for (int k = 0; k < n; ++k) pack_params(model, k, pstride, params.data());
+    FwdIO io;
+    memset(&io, 0, sizeof io);
+    io.g64 = grids;
+    io.counts = counts;
+    io.dump = (dump && dump->count > 0) ? dump : nullptr;
+    return forward_common(ctx, d, n, model->N, model->m, params.data(), M, seed, &o, kSampler, io, stats,
+                          (cudaStream_t)stream);
+}
+
+extern "C" qt_status qt_counts_from_samples(qt_ctx* ctx, int32_t d, const double* gA, int64_t NA, const double* gB,
+                                            int64_t NB, const double* X, const double* Y, int64_t M,
+                                            const qt_options* opts, void* counts, int32_t* ii, int32_t* jj,
+                                            qt_stats* stats, void* stream)
+{
+    if (!ctx) return QT_EINVAL;
+    if (d < 1 || d > kDMax) return fail(ctx, QT_EINVAL, "d = %d outside [1, %d]", d, kDMax);
+    if (!gA || !gB || !X || !Y || !counts) return fail(ctx, QT_EINVAL, "NULL array");
+    if (NA < 1 || NB < 1 || NA > (1 << 24) || NB > (1 << 24)) return fail(ctx, QT_EINVAL, "grid sizes");
+    if (M < 1 || M > 0xFFFFFFFFll) return fail(ctx, QT_EINVAL, "M = %lld outside [1, 2^32)", (long long)M);
+    if ((ii == nullptr) != (jj == nullptr)) return fail(ctx, QT_EINVAL, "ii and jj must both be set or both NULL");
+    qt_options o;
+    if (opts) o = *opts; else qt_default_options(&o);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // both grids contiguous in one workspace buffer
+    void* dg;
+    qt_status s = dev_get(ctx, "pair_grids", sizeof(double) * (size_t)(NA + NB) * d, &dg);
+    if (s) return s;
+    QT_CUDA(cudaMemcpyAsync(dg, gA, sizeof(double) * NA * d, cudaMemcpyDeviceToDevice, st));
+    QT_CUDA(cudaMemcpyAsync((double*)dg + NA * d, gB, sizeof(double) * NB * d, cudaMemcpyDeviceToDevice, st));
+    // centres of the screen: zero (the bound uses the norms about this centre)
+    std::vector<double> mus((size_t)2 * d, 0.0);
+    int64_t Ns[2] = {NA, NB};
+    FwdIO io;
+    memset(&io, 0, sizeof io);
+    io.g64 = (const double*)dg;
+    io.counts = counts;
+    io.srcX = X;
+    io.srcY = Y;
+    io.cellsA = ii;
+    io.cellsB = jj;
+    o.sample_prec = QT_PREC_F64;
+    o.flags |= QT_FLAG_NO_GRAPH;
+    return forward_common(ctx, d, 1, Ns, mus.data(), nullptr, M, 0, &o, kArrays, io, stats, st);
+}
+
+extern "C" qt_status qt_get_status(qt_ctx* ctx, void* stream, qt_stats* stats)
+{
+    if (!ctx) return QT_EINVAL;
+    DeviceGuard g(ctx->device);
+    return read_status(ctx, (cudaStream_t)stream, stats, 0, 0);
+}
+
+extern "C" qt_status qt_transitions_workspace(const qt_model* model, const qt_options* opts, size_t* bytes)
+{
+    if (!model || !bytes || model->d < 1 || model->d > kDMax || model->n < 1) return QT_EINVAL;
+    qt_options o;
+    if (opts) o = *opts; else qt_default_options(&o);
+    const int d = model->d, n = model->n, dm = dm_for(d);
+    long long recs = 0;
+    for (int k = 0; k <= n; ++k) recs += round_up(model->N[k], kChunk);
+    const long long pstride = round_up(2 * d + 3 * d * d, 4);
+    size_t b = sizeof(LayerDesc) * n + sizeof(GridInfo) * (n + 1) + (size_t)n * pstride * 12 + sizeof(DevStatus);
+    b += o.form == QT_FORM_PLAIN_F64 ? (size_t)recs * rec64_for(dm) * 8 : (size_t)recs * rec_floats_for(dm) * 4;
+    *bytes = b;
+    return QT_OK;
+}
+
+// ------------------------------------------------------------------ backward induction and price
+
+extern "C" qt_status qt_backward(qt_ctx* ctx, int32_t n, const int64_t* N, const void* counts, int32_t counts_type,
+                                 const double* phi, double* V, void* stream)
+{
+    if (!ctx) return QT_EINVAL;
+    if (n < 1 || !N || !counts || !phi || !V) return fail(ctx, QT_EINVAL, "bad arguments to qt_backward");
+    if (counts_type != QT_COUNTS_I64 && counts_type != QT_COUNTS_U32)
+        return fail(ctx, QT_EINVAL, "counts_type %d", counts_type);
+    for (int k = 0; k <= n; ++k)
+        if (N[k] < 1 || N[k] > (1 << 24)) return fail(ctx, QT_EINVAL, "N[%d]", k);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<long long> goff(n + 2, 0), coff(n + 1, 0);
+    for (int k = 0; k <= n; ++k) goff[k + 1] = goff[k] + N[k];
+    for (int k = 0; k < n; ++k) coff[k + 1] = coff[k] + N[k] * N[k + 1];
+    QT_CUDA(cudaMemcpyAsync(V + goff[n], phi + goff[n], sizeof(double) * N[n], cudaMemcpyDeviceToDevice, st));
+    const int u32 = counts_type == QT_COUNTS_U32;
+    for (int k = n - 1; k >= 0; --k) {
+        const long long threads = (long long)N[k] * 32;
+        const int blk = 256;
+        backward_layer_kernel<<<(unsigned)((threads + blk - 1) / blk), blk, 0, st>>>(
+            counts, u32, coff[k], (int)N[k], (int)N[k + 1], phi + goff[k], V + goff[k + 1], V + goff[k]);
+        QT_CUDA(cudaGetLastError());
+    }
+    return QT_OK;
+}
+
+namespace {
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+extern "C" qt_status qt_price(qt_ctx* ctx, const qt_model* model, const double* grids, int64_t M, uint64_t seed,
+                              const qt_options* opts, const double* phi, double* price, qt_stats* stats, void* stream)
+{
+    if (!ctx) return QT_EINVAL;
+    qt_status s = validate_model(ctx, model);
+    if (s) return s;
+    if (!grids || !phi || !price) return fail(ctx, QT_EINVAL, "NULL argument to qt_price");
+    qt_options o;
+    if (opts) o = *opts; else qt_default_options(&o);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = model->n, d = model->d;
+    long long pts = 0, ent = 0;
+    for (int k = 0; k <= n; ++k) pts += model->N[k];
+    for (int k = 0; k < n; ++k) ent += model->N[k] * model->N[k + 1];
+    const size_t csize = o.counts_type == QT_COUNTS_U32 ? 4 : 8;
+    void *dcounts, *dV, *dout;
+    if ((s = dev_get(ctx, "price_counts", csize * (size_t)ent, &dcounts))) return s;
+    if ((s = dev_get(ctx, "price_V", sizeof(double) * (size_t)pts, &dV))) return s;
+    if ((s = dev_get(ctx, "price_out", sizeof(double), &dout))) return s;
+    const double* dgrids = grids;
+    const double* dphi = phi;
+    if (!is_device_ptr(grids)) {
+        void* p;
+        if ((s = dev_get(ctx, "price_grids", sizeof(double) * (size_t)pts * d, &p))) return s;
+        QT_CUDA(cudaMemcpyAsync(p, grids, sizeof(double) * (size_t)pts * d, cudaMemcpyHostToDevice, st));
+        dgrids = (const double*)p;
+    }
+    if (!is_device_ptr(phi)) {
+        void* p;
+        if ((s = dev_get(ctx, "price_phi", sizeof(double) * (size_t)pts, &p))) return s;
+        QT_CUDA(cudaMemcpyAsync(p, phi, sizeof(double) * (size_t)pts, cudaMemcpyHostToDevice, st));
+        dphi = (const double*)p;
+    }
+    if ((s = qt_transitions(ctx, model, dgrids, M, seed, &o, dcounts, nullptr, nullptr, stream))) return s;
+    if ((s = qt_backward(ctx, n, model->N, dcounts, o.counts_type, dphi, (double*)dV, stream))) return s;
+    root_price_kernel<<<1, 32, 0, st>>>(dcounts, o.counts_type == QT_COUNTS_U32, (int)model->N[0], (int)model->N[1],
+                                        (const double*)dV, (double*)dout);
+    QT_CUDA(cudaGetLastError());
+    QT_CUDA(cudaMemcpyAsync(price, dout, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return read_status(ctx, st, stats, (long long)n * M, 2ll * n * M);
+}
+
+// ------------------------------------------------------------------ grid builder
+
+namespace {
+
+double npdf(double z) { return std::isfinite(z) ? std::exp(-0.5 * z * z) * 0.3989422804014327 : 0.0; }
+double ncdf_upper(double z) { return 0.5 * std::erfc(z * 0.7071067811865476); }   // P(Z > z)
+double cell_mass(double lo, double hi)
+{
+    return hi <= 0 ? ncdf_upper(-hi) - ncdf_upper(-lo) : ncdf_upper(lo) - ncdf_upper(hi);
+}
+
+// Stationary N-point quantizer of N(0,1): Lloyd's map on closed-form cell
+// means, then Newton on G_i = x_i P_i - (pdf(b_{i-1}) - pdf(b_i)) (tridiagonal).
+std::vector<double> lloyd1d(int N, double tol)
+{
+    std::vector<double> x(N, 0.0);
+    if (N == 1) return x;
+    // quantile start via bisection on the upper tail
+    for (int i = 0; i < N; ++i) {
+        const double p = (i + 0.5) / N;
+        double lo = -10, hi = 10;
+        for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (1.0 - ncdf_upper(mid) < p) lo = mid; else hi = mid;
+        }
+        x[i] = 0.5 * (lo + hi);
+    }
+    std::vector<double> lo(N), hi(N), P(N), Q(N), G(N), a(N), b(N), c(N), step(N);
+    auto cells = [&]() {
+        for (int i = 0; i < N; ++i) {
+            lo[i] = i == 0 ? -INFINITY : 0.5 * (x[i - 1] + x[i]);
+            hi[i] = i == N - 1 ? INFINITY : 0.5 * (x[i] + x[i + 1]);
+            P[i] = cell_mass(lo[i], hi[i]);
+            Q[i] = npdf(lo[i]) - npdf(hi[i]);
+        }
+    };
+    for (int it = 0; it < 200; ++it) {
+        cells();
+        for (int i = 0; i < N; ++i) x[i] = Q[i] / P[i];
+    }
+    for (int it = 0; it < 100; ++it) {
+        cells();
+        for (int i = 0; i < N; ++i) {
+            G[i] = x[i] * P[i] - Q[i];
+            const double lf = std::isfinite(lo[i]) ? lo[i] : 0.0, hf = std::isfinite(hi[i]) ? hi[i] : 0.0;
+            b[i] = P[i] + 0.5 * (x[i] - hf) * npdf(hi[i]) + 0.5 * (lf - x[i]) * npdf(lo[i]);
+            c[i] = i < N - 1 ? 0.5 * (x[i] - hf) * npdf(hi[i]) : 0.0;
+            a[i] = i > 0 ? 0.5 * (lf - x[i]) * npdf(lo[i]) : 0.0;
+        }
+        // Thomas algorithm
+        std::vector<double> cp(N), dp(N);
+        cp[0] = c[0] / b[0];
+        dp[0] = G[0] / b[0];
+        for (int i = 1; i < N; ++i) {
+            const double den = b[i] - a[i] * cp[i - 1];
+            cp[i] = c[i] / den;
+            dp[i] = (G[i] - a[i] * dp[i - 1]) / den;
+        }
+        step[N - 1] = dp[N - 1];
+        for (int i = N - 2; i >= 0; --i) step[i] = dp[i] - cp[i] * step[i + 1];
+        double mx = 0;
+        for (int i = 0; i < N; ++i) {
+            x[i] -= step[i];
+            mx = std::max(mx, std::fabs(step[i]));
+        }
+        for (int i = 0; i < N / 2; ++i) {  // exact symmetry of the optimum
+            const double v = 0.5 * (x[N - 1 - i] - x[i]);
+            x[i] = -v;
+            x[N - 1 - i] = v;
+        }
+        if (N % 2) x[N / 2] = 0.0;
+        if (mx < tol) break;
+    }
+    return x;
+}
+
+void factor_sizes(int N, int d, std::vector<int>& best, std::vector<int>& cur, double& score)
+{
+    if (d == 1) {
+        cur.push_back(N);
+        int mx = *std::max_element(cur.begin(), cur.end()), mn = *std::min_element(cur.begin(), cur.end());
+        const double sc = (double)mx / mn;
+        if (best.empty() || sc < score) {
+            score = sc;
+            best = cur;
+        }
+        cur.pop_back();
+        return;
+    }
+    for (int a = 1; a <= N; ++a) {
+        if (N % a) continue;
+        cur.push_back(a);
+        factor_sizes(N / a, d - 1, best, cur, score);
+        cur.pop_back();
+    }
+}
+
+}  // namespace
+
+extern "C" qt_status qt_build_grids(qt_ctx* ctx, const qt_model* model, int32_t method, int64_t samples, int32_t iters,
+                                    double tol, uint64_t seed, double* grids, void* stream)
+{
+    if (!ctx) return QT_EINVAL;
+    qt_status s = validate_model(ctx, model);
+    if (s) return s;
+    if (!grids) return fail(ctx, QT_EINVAL, "grids is NULL");
+    const int d = model->d, n = model->n;
+    if (method == QT_GRID_LLOYD1D && d != 1) return fail(ctx, QT_EINVAL, "QT_GRID_LLOYD1D needs d = 1");
+    if (method != QT_GRID_LLOYD1D && method != QT_GRID_PRODUCT && method != QT_GRID_KMEANS)
+        return fail(ctx, QT_EINVAL, "unknown grid method %d", method);
+    if (tol <= 0) tol = 1e-14;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::map<long long, std::vector<double>> base;   // N -> base grid of N(0, I_d), [N][d]
+    for (int k = 0; k <= n; ++k) {
+        const long long Nk = model->N[k];
+        if (base.count(Nk)) continue;
+        std::vector<double> G((size_t)Nk * d, 0.0);
+        if (Nk == 1) {
+            // the single point is the mean
+        } else if (method == QT_GRID_LLOYD1D) {
+            std::vector<double> x = lloyd1d((int)Nk, tol);
+            for (long long j = 0; j < Nk; ++j) G[j] = x[j];
+        } else if (method == QT_GRID_PRODUCT) {
+            std::vector<int> best, cur;
+            double score = 0;
+            factor_sizes((int)Nk, d, best, cur, score);
+            std::sort(best.begin(), best.end());
+            std::vector<std::vector<double>> ax;
+            for (int l = 0; l < d; ++l) ax.push_back(lloyd1d(best[l], tol));
+            for (long long j = 0; j < Nk; ++j) {
+                long long r = j;
+                for (int l = d - 1; l >= 0; --l) {
+                    G[j * d + l] = ax[l][r % best[l]];
+                    r /= best[l];
+                }
+            }
+        } else {
+            const long long S = samples > 0 ? samples : std::max<long long>(20 * Nk, 100000);
+            const int its = iters > 0 ? iters : 20;
+            if (S < Nk) return fail(ctx, QT_EINVAL, "k-means needs at least N training samples");
+            void *dZ, *dC, *dsum, *dcnt;
+            if ((s = dev_get(ctx, "km_Z", sizeof(float) * (size_t)S * d, &dZ))) return s;
+            if ((s = dev_get(ctx, "km_C", sizeof(float) * (size_t)Nk * d, &dC))) return s;
+            if ((s = dev_get(ctx, "km_sum", 8 * (size_t)Nk * d, &dsum))) return s;
+            if ((s = dev_get(ctx, "km_cnt", 8 * (size_t)Nk, &dcnt))) return s;
+            const unsigned long long kseed = seed ^ (0x9E3779B97F4A7C15ull * (unsigned long long)Nk);
+            kmeans_draw_kernel<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(d, kseed, S, (float*)dZ);
+            QT_CUDA(cudaGetLastError());
+            QT_CUDA(cudaMemcpyAsync(dC, dZ, sizeof(float) * (size_t)Nk * d, cudaMemcpyDeviceToDevice, st));
+            const size_t csm = sizeof(float) * (size_t)Nk * d;
+            const int use_smem = csm <= 160 * 1024;
+            if (use_smem)
+                QT_CUDA(cudaFuncSetAttribute(kmeans_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)csm));
+            for (int it = 0; it < its; ++it) {
+                QT_CUDA(cudaMemsetAsync(dsum, 0, 8 * (size_t)Nk * d, st));
+                QT_CUDA(cudaMemsetAsync(dcnt, 0, 8 * (size_t)Nk, st));
+                kmeans_assign_kernel<<<(unsigned)((S + 255) / 256), 256, use_smem ? csm : 0, st>>>(
+                    d, S, (const float*)dZ, (int)Nk, (const float*)dC, (unsigned long long*)dsum,
+                    (unsigned long long*)dcnt, use_smem);
+                QT_CUDA(cudaGetLastError());
+                kmeans_update_kernel<<<(unsigned)((Nk + 255) / 256), 256, 0, st>>>(
+                    d, (int)Nk, (const unsigned long long*)dsum, (const unsigned long long*)dcnt, (float*)dC);
+                QT_CUDA(cudaGetLastError());
+            }
+            std::vector<float> Gf((size_t)Nk * d);
+            QT_CUDA(cudaMemcpyAsync(Gf.data(), dC, csm, cudaMemcpyDeviceToHost, st));
+            QT_CUDA(cudaStreamSynchronize(st));
+            for (size_t e = 0; e < Gf.size(); ++e) G[e] = (double)Gf[e];
+        }
+        base[Nk] = std::move(G);
+    }
+    // map every layer: x = m_k + L_k g
+    long long off = 0;
+    void *dG, *dm, *dL;
+    long long maxN = 0;
+    for (int k = 0; k <= n; ++k) maxN = std::max<long long>(maxN, model->N[k]);
+    if ((s = dev_get(ctx, "bg_G", sizeof(double) * (size_t)maxN * d, &dG))) return s;
+    if ((s = dev_get(ctx, "bg_m", sizeof(double) * d, &dm))) return s;
+    if ((s = dev_get(ctx, "bg_L", sizeof(double) * d * d, &dL))) return s;
+    for (int k = 0; k <= n; ++k) {
+        const long long Nk = model->N[k];
+        const std::vector<double>& G = base[Nk];
+        QT_CUDA(cudaMemcpyAsync(dG, G.data(), sizeof(double) * (size_t)Nk * d, cudaMemcpyHostToDevice, st));
+        QT_CUDA(cudaMemcpyAsync(dm, model->m + (long long)k * d, sizeof(double) * d, cudaMemcpyHostToDevice, st));
+        QT_CUDA(cudaMemcpyAsync(dL, model->L + (long long)k * d * d, sizeof(double) * d * d, cudaMemcpyHostToDevice, st));
+        map_grid_kernel<<<(unsigned)((Nk + 255) / 256), 256, 0, st>>>(d, (int)Nk, (const double*)dG,
+                                                                    (const double*)dm, (const double*)dL,
+                                                                    grids + off * d);
+        QT_CUDA(cudaGetLastError());
+        QT_CUDA(cudaStreamSynchronize(st));  // the staging buffers are reused next layer
+        off += Nk;
+    }
+    return QT_OK;
+}

@@ -1,0 +1,643 @@
+// qt_forward.cuh -- the forward step of the Quantization Tree algorithm
+// (Algorithm III of Pages & Wilbertz, arXiv:1101.3228, Sec. 4) as one
+// persistent kernel over all layers.
+//
+// Work item = (layer k, tile of samples).  Items are ordered layer by layer and
+// handed out by an atomic counter, so uneven grid sizes N_k balance by
+// themselves (the paper runs one block per layer; Sec. 4, remark after
+// Algorithm III).  On a layer switch a CTA stages Gamma_k and Gamma_{k+1} into
+// shared memory with bulk TMA copies (cp.async.bulk + mbarrier), which is the
+// GB300 form of the paper's "grids in shared memory" design.
+//
+// Per sample: draw (X_k, eps_k) (qt_sampler.cuh), search the nearest cell of
+// X_k in Gamma_k and of Y = A_k X_k + b_k + T_k eps_k in Gamma_{k+1} (Sec. 3.2,
+// brute force as the paper chose), then add 1 to p^k_ij (Sec. 3.3: atomics;
+// here a shared-memory private histogram or red.global.add into L2).
+//
+// Search forms:
+//  * plain FP64: the exact distance D64 of the library contract, strict '<'
+//    over ascending indices (ties to the lowest index);
+//  * FP32 screen: scores s_j = |c_j - mu|^2 - 2 (x - mu).(c_j - mu) with FMA
+//    chains on centred FP32 copies; the running minimum is tracked per chunk of
+//    kChunk candidates (one 3-input min per candidate pair), the best chunk is
+//    re-scored at the end for the index and the second-best score.  A sample is
+//    certified when  s_2nd - s_best > (d+2) (R + |x^|)^2 2^-22,  twice a bound
+//    on |s~_j - s_j| plus the FP64 rounding of the exact distance (R = max norm
+//    of the centred grid, x^ the centred sample).  Uncertified samples are
+//    re-evaluated exactly in FP64 by the whole warp.
+#pragma once
+#include <cstdint>
+#include <cfloat>
+
+#include "qt_internal.h"
+#include "qt_sampler.cuh"
+
+namespace qt {
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// 1-D bulk copy global -> shared, completion counted on the mbarrier.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: at most `budget` polls; budget < 0 gives up without polling.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long budget)
+{
+    if (budget < 0) return false;
+    for (long long it = 0; it <= budget; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ void record_error(DevStatus* st, int code, int where)
+{
+    if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
+}
+
+__device__ __forceinline__ void count_add(void* counts, int u32, long long e, uint32_t v)
+{
+    if (u32) {
+        asm volatile("red.global.add.u32 [%0], %1;" ::"l"((uint32_t*)counts + e), "r"(v) : "memory");
+    } else {
+        asm volatile("red.global.add.u64 [%0], %1;" ::"l"((unsigned long long*)counts + e),
+                     "l"((unsigned long long)v)
+                     : "memory");
+    }
+}
+
+// Exact distance of the library contract: sum_l (z_l - x_l)^2, left to right,
+// binary64, round to nearest, no contraction.
+template <int DM>
+__device__ __forceinline__ double dist64(const double (&z)[DM], const double* __restrict__ x, int d)
+{
+    double acc = 0.0;
+#pragma unroll
+    for (int l = 0; l < DM; ++l) {
+        if (l < d) {
+            const double t = __dsub_rn(z[l], x[l]);
+            acc = __dadd_rn(acc, __dmul_rn(t, t));
+        }
+    }
+    return acc;
+}
+
+// Records of the FP32 screen: [cc, c_0 .. c_{DM-1}, 0 ...] rounded up to float4.
+template <int DM>
+struct Rec32 {
+    static constexpr int kVec = (DM + 1 + 3) / 4;
+    static constexpr int kFloats = 4 * kVec;
+};
+template <int DM>
+struct Rec64 {
+    static constexpr int kDoubles = (DM + 1) / 2 * 2;
+};
+
+// ------------------------------------------------------------------ sample access
+
+struct TileCtx {
+    const LayerDesc* L;      // shared-memory copy of the current layer descriptor
+    int k;
+    unsigned long long m0;   // first sample of the tile
+};
+
+// Exact sample (X or Y) of sample m as FP64 (regenerated for rechecks and dumps).
+template <int DM>
+__device__ __noinline__ void exact_sample(const ForwardParams& p, const float* spf, const double* spd, int k,
+                                             unsigned long long m, bool wantY, double (&z)[DM])
+{
+    if (p.source == kArrays) {
+        const double* src = wantY ? p.srcY : p.srcX;
+#pragma unroll
+        for (int l = 0; l < DM; ++l) z[l] = (l < p.d) ? src[m * (unsigned long long)p.d + l] : 0.0;
+        return;
+    }
+    if (p.prec == 1) {
+        float X[DM], Y[DM];
+        pair_f32<DM>(spf, p.d, p.seed, k, m, X, Y);
+#pragma unroll
+        for (int l = 0; l < DM; ++l) z[l] = (double)(wantY ? Y[l] : X[l]);
+    } else {
+        double X[DM], Y[DM];
+        pair_f64<DM>(spd, p.d, p.seed, k, m, X, Y);
+#pragma unroll
+        for (int l = 0; l < DM; ++l) z[l] = wantY ? Y[l] : X[l];
+    }
+}
+
+// Warp-cooperative exact search for one lane's point z (broadcast from `src`):
+// lanes scan j = lane, lane+32, ... and the warp reduces (D64, j) lexicographically.
+template <int DM>
+__device__ __noinline__ int warp_exact_nn(const double (&z)[DM], int src_lane, const double* __restrict__ g,
+                                             int N, int d)
+{
+    double zz[DM];
+#pragma unroll
+    for (int l = 0; l < DM; ++l) zz[l] = __shfl_sync(0xFFFFFFFFu, z[l], src_lane);
+    const int lane = threadIdx.x & 31;
+    double best = __longlong_as_double(0x7FF0000000000000LL);  // +inf
+    int bi = 0x7FFFFFFF;
+    for (int j = lane; j < N; j += 32) {
+        const double dj = dist64<DM>(zz, g + (long long)j * d, d);
+        if (dj < best) {  // ascending j per lane: strict '<' keeps the lowest index
+            best = dj;
+            bi = j;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const double ob = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+        const int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, off);
+        if (ob < best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+        }
+    }
+    return bi;
+}
+
+// ------------------------------------------------------------------ FP32 screen
+
+template <int DM>
+struct Centred {
+    float xa[DM], yb[DM];  // -2 (X - mu_A), -2 (Y - mu_B) in FP32
+    float Aa, Ab;          // |X - mu_A|, |Y - mu_B| of the rounded centred values
+};
+
+// Draw (or load) sample m and centre it on the two grids.
+template <int DM>
+__device__ __noinline__ Centred<DM> centred_sample(const ForwardParams& p, const float* spf, const double* spd,
+                                                   const float* muA, const float* muB, int k, unsigned long long m)
+{
+    Centred<DM> c;
+    const int d = p.d;
+    float na = 0.f, nb = 0.f;
+    if (p.source == kSampler && p.prec == 1) {
+        float X[DM], Y[DM];
+        pair_f32<DM>(spf, d, p.seed, k, m, X, Y);
+#pragma unroll
+        for (int l = 0; l < DM; ++l) {
+            const float ax = __fsub_rn(X[l], muA[l]);
+            const float by = __fsub_rn(Y[l], muB[l]);
+            na = __fmaf_rn(ax, ax, na);
+            nb = __fmaf_rn(by, by, nb);
+            c.xa[l] = -2.0f * ax;
+            c.yb[l] = -2.0f * by;
+        }
+    } else {
+        double X[DM], Y[DM];
+        if (p.source == kSampler) {
+            pair_f64<DM>(spd, d, p.seed, k, m, X, Y);
+        } else {
+#pragma unroll
+            for (int l = 0; l < DM; ++l) {
+                X[l] = (l < d) ? p.srcX[m * (unsigned long long)d + l] : 0.0;
+                Y[l] = (l < d) ? p.srcY[m * (unsigned long long)d + l] : 0.0;
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < DM; ++l) {
+            const float ax = __double2float_rn(__dsub_rn(X[l], (double)muA[l]));
+            const float by = __double2float_rn(__dsub_rn(Y[l], (double)muB[l]));
+            na = __fmaf_rn(ax, ax, na);
+            nb = __fmaf_rn(by, by, nb);
+            c.xa[l] = -2.0f * ax;
+            c.yb[l] = -2.0f * by;
+        }
+    }
+    c.Aa = __fsqrt_rn(na);
+    c.Ab = __fsqrt_rn(nb);
+    return c;
+}
+
+// Exact FP64 pair for the plain form.
+template <int DM>
+struct Exact {
+    double X[DM], Y[DM];
+};
+
+template <int DM>
+__device__ __noinline__ Exact<DM> exact_pair(const ForwardParams& p, const float* spf, const double* spd, int k,
+                                             unsigned long long m)
+{
+    Exact<DM> e;
+    const int d = p.d;
+    if (p.source == kArrays) {
+#pragma unroll
+        for (int l = 0; l < DM; ++l) {
+            e.X[l] = (l < d) ? p.srcX[m * (unsigned long long)d + l] : 0.0;
+            e.Y[l] = (l < d) ? p.srcY[m * (unsigned long long)d + l] : 0.0;
+        }
+    } else if (p.prec == 1) {
+        float Xf[DM], Yf[DM];
+        pair_f32<DM>(spf, d, p.seed, k, m, Xf, Yf);
+#pragma unroll
+        for (int l = 0; l < DM; ++l) {
+            e.X[l] = (double)Xf[l];
+            e.Y[l] = (double)Yf[l];
+        }
+    } else {
+        pair_f64<DM>(spd, d, p.seed, k, m, e.X, e.Y);
+    }
+    return e;
+}
+
+// Scan `nchunk` chunks of records for S centred, scaled samples xs (xs = -2 x^).
+template <int DM, int S>
+__device__ __forceinline__ void screen_scan(const float* __restrict__ recs, int nchunk, const float (&xs)[S][DM],
+                                            float (&B1)[S], float (&B2)[S], int (&bc)[S])
+{
+    constexpr int V = Rec32<DM>::kVec;
+    const float4* r4 = reinterpret_cast<const float4*>(recs);
+    for (int c = 0; c < nchunk; ++c) {
+        float mc[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) mc[s] = __int_as_float(0x7F800000);
+#pragma unroll 2
+        for (int q = 0; q < kChunk; q += 2) {
+            float ra[4 * V], rb[4 * V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float4 a = r4[(c * kChunk + q) * V + v];
+                const float4 b = r4[(c * kChunk + q + 1) * V + v];
+                ra[4 * v + 0] = a.x; ra[4 * v + 1] = a.y; ra[4 * v + 2] = a.z; ra[4 * v + 3] = a.w;
+                rb[4 * v + 0] = b.x; rb[4 * v + 1] = b.y; rb[4 * v + 2] = b.z; rb[4 * v + 3] = b.w;
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                float sa = ra[0], sb = rb[0];
+#pragma unroll
+                for (int l = 0; l < DM; ++l) {
+                    sa = __fmaf_rn(xs[s][l], ra[1 + l], sa);
+                    sb = __fmaf_rn(xs[s][l], rb[1 + l], sb);
+                }
+                mc[s] = min3f(mc[s], sa, sb);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            B2[s] = fminf(B2[s], fmaxf(mc[s], B1[s]));
+            const bool nw = mc[s] < B1[s];
+            B1[s] = fminf(B1[s], mc[s]);
+            bc[s] = nw ? c : bc[s];
+        }
+    }
+}
+
+// Re-score the best chunk of one sample: lowest index achieving B1 and the
+// smallest other score of that chunk.
+template <int DM>
+__device__ __forceinline__ void screen_resolve(const float* __restrict__ recs, int chunk, const float (&x)[DM],
+                                               float B1, int& idx, float& S1)
+{
+    constexpr int F = Rec32<DM>::kFloats;
+    idx = -1;
+    S1 = __int_as_float(0x7F800000);
+    for (int q = 0; q < kChunk; ++q) {
+        const float* r = recs + (chunk * kChunk + q) * F;
+        float sc = r[0];
+#pragma unroll
+        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], r[1 + l], sc);
+        if (sc == B1 && idx < 0) {
+            idx = chunk * kChunk + q;
+        } else {
+            S1 = fminf(S1, sc);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ the kernel
+
+template <int DM, int S, int FORM>
+__global__ void __launch_bounds__(256) forward_kernel(const ForwardParams p)
+{
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(8) unsigned long long s_bar;
+    __shared__ long long s_item;
+    __shared__ LayerDesc s_L;
+    __shared__ GridInfo s_GA, s_GB;
+    __shared__ __align__(16) float s_pf[param_count(DM)];
+    __shared__ __align__(16) double s_pd[param_count(DM)];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int d = p.d;
+    const uint32_t bar = smem_u32(&s_bar);
+    unsigned char* grid_sm = dsm;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(dsm + p.smem_grid_bytes);
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_proxy_async();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    int cur = -1;
+    uint32_t phase = 0;
+    bool hist_live = false;
+
+    while (true) {
+        if (tid == 0) {
+            long long it = -1;
+            if (*((volatile int32_t*)&p.status->code) == 0)
+                it = (long long)atomicAdd(&p.status->queue, 1ull);
+            s_item = it;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item < 0 || item >= p.total_items) break;
+
+        // ---- locate the layer of this item (items are grouped layer by layer)
+        int k = (cur >= 0 && item >= s_L.item_begin && item < s_L.item_begin + s_L.items) ? cur : -1;
+        if (k < 0) {
+            int lo = 0, hi = p.n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (p.layers[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+            }
+            k = lo;
+        }
+
+        if (k != cur) {
+            // ---- flush the private histogram of the previous layer
+            if (hist_live) {
+                const int ent = s_L.NA * s_L.NB;
+                for (int e = tid; e < ent; e += blockDim.x) {
+                    const uint32_t v = hist[e];
+                    if (v) {
+                        count_add(p.counts, p.counts_u32, s_L.coff + e, v);
+                        hist[e] = 0;
+                    }
+                }
+                hist_live = false;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                s_L = p.layers[k];
+                s_GA = p.grids[s_L.gridA];
+                s_GB = p.grids[s_L.gridB];
+            }
+            __syncthreads();
+            // ---- stage both grids with bulk copies (TMA engine)
+            if (tid == 0) {
+                uint32_t bytesA, bytesB;
+                const void *srcA, *srcB;
+                if (FORM == kF32Recheck) {
+                    bytesA = (uint32_t)s_L.NApad * Rec32<DM>::kFloats * 4u;
+                    bytesB = (uint32_t)s_L.NBpad * Rec32<DM>::kFloats * 4u;
+                    srcA = p.rec32 + s_L.roffA * Rec32<DM>::kFloats;
+                    srcB = p.rec32 + s_L.roffB * Rec32<DM>::kFloats;
+                } else {
+                    bytesA = (uint32_t)s_L.NApad * Rec64<DM>::kDoubles * 8u;
+                    bytesB = (uint32_t)s_L.NBpad * Rec64<DM>::kDoubles * 8u;
+                    srcA = p.rec64 + s_L.roffA * Rec64<DM>::kDoubles;
+                    srcB = p.rec64 + s_L.roffB * Rec64<DM>::kDoubles;
+                }
+                fence_proxy_async();
+                mbar_arrive_expect_tx(bar, bytesA + bytesB);
+                bulk_g2s(smem_u32(grid_sm), srcA, bytesA, bar);
+                bulk_g2s(smem_u32(grid_sm + bytesA), srcB, bytesB, bar);
+            }
+            // ---- sampler parameters and private histogram
+            if (p.source == kSampler) {
+                const int pc = param_count(d);
+                for (int e = tid; e < pc; e += blockDim.x) {
+                    s_pf[e] = p.params_f[(long long)k * p.params_stride + e];
+                    s_pd[e] = p.params_d[(long long)k * p.params_stride + e];
+                }
+            }
+            if (s_L.hist_smem) {
+                const int ent = s_L.NA * s_L.NB;
+                for (int e = tid; e < ent; e += blockDim.x) hist[e] = 0;
+                hist_live = true;
+            }
+            // ---- wait for the grids (bounded)
+            const bool ok = mbar_wait_bounded(bar, phase, p.spin_budget);
+            if (!ok) {
+                // give up: record the timeout, let the copies land (bounded, fixed
+                // budget), then leave the kernel without touching the results
+                if (tid == 0) {
+                    record_error(p.status, 4 /* QT_ETIMEOUT */, 1);
+                    s_abort = 1;
+                }
+                mbar_wait_bounded(bar, phase, 1ll << 24);
+            }
+            phase ^= 1u;
+            __syncthreads();
+            if (s_abort) break;
+            cur = k;
+        }
+
+        const LayerDesc& L = s_L;
+        const unsigned long long mtile = (unsigned long long)(item - L.item_begin) * (unsigned long long)p.tile;
+        unsigned long long ms[S];
+        bool valid[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            ms[s] = mtile + (unsigned long long)(s * blockDim.x + tid);
+            valid[s] = ms[s] < p.M;
+        }
+
+        int ci[S], cj[S];
+
+        if (FORM == kF32Recheck) {
+            // ---- centred, scaled FP32 copies of X (grid A) and Y (grid B)
+            float xa[S][DM], yb[S][DM];
+            float Aa[S], Ab[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const unsigned long long m = valid[s] ? ms[s] : mtile;
+                const Centred<DM> c = centred_sample<DM>(p, s_pf, s_pd, s_GA.mu, s_GB.mu, k, m);
+#pragma unroll
+                for (int l = 0; l < DM; ++l) {
+                    xa[s][l] = c.xa[l];
+                    yb[s][l] = c.yb[l];
+                }
+                Aa[s] = c.Aa;
+                Ab[s] = c.Ab;
+            }
+            const float* recA = reinterpret_cast<const float*>(grid_sm);
+            const float* recB = recA + (long long)L.NApad * Rec32<DM>::kFloats;
+            bool needA[S], needB[S];
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                const float* rec = g == 0 ? recA : recB;
+                const int nch = (g == 0 ? L.NApad : L.NBpad) / kChunk;
+                const float R = g == 0 ? s_GA.R : s_GB.R;
+                float B1[S], B2[S];
+                int bc[S];
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    B1[s] = __int_as_float(0x7F800000);
+                    B2[s] = __int_as_float(0x7F800000);
+                    bc[s] = 0;
+                }
+                if (g == 0) screen_scan<DM, S>(rec, nch, xa, B1, B2, bc);
+                else screen_scan<DM, S>(rec, nch, yb, B1, B2, bc);
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    int idx;
+                    float S1;
+                    if (g == 0) screen_resolve<DM>(rec, bc[s], xa[s], B1[s], idx, S1);
+                    else screen_resolve<DM>(rec, bc[s], yb[s], B1[s], idx, S1);
+                    const float second = fminf(B2[s], S1);
+                    const float A = g == 0 ? Aa[s] : Ab[s];
+                    const float rr = R + A;
+                    const float thr = (float)(d + 2) * (rr * rr) * 0x1p-22f;
+                    const bool cert = (second - B1[s]) > thr && idx >= 0;
+                    if (g == 0) {
+                        ci[s] = idx;
+                        needA[s] = !cert && valid[s];
+                    } else {
+                        cj[s] = idx;
+                        needB[s] = !cert && valid[s];
+                    }
+                }
+            }
+            // ---- exact FP64 recheck of uncertified searches, one warp per search
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const bool need = g == 0 ? needA[s] : needB[s];
+                    unsigned mask = __ballot_sync(0xFFFFFFFFu, need);
+                    if (mask == 0) continue;
+                    double z[DM];
+                    if (need) exact_sample<DM>(p, s_pf, s_pd, k, ms[s], g == 1, z);
+                    const double* g64 = p.g64 + (g == 0 ? s_GA.goff : s_GB.goff) * d;
+                    const int N = g == 0 ? L.NA : L.NB;
+                    while (mask) {
+                        const int src = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const int r = warp_exact_nn<DM>(z, src, g64, N, d);
+                        if (lane == src) {
+                            if (g == 0) ci[s] = r; else cj[s] = r;
+                        }
+                        if (lane == 0) atomicAdd(&p.status->rechecks, 1ull);
+                    }
+                }
+            }
+        } else {
+            // ---- plain FP64 brute force (exact by construction)
+            constexpr int R64 = Rec64<DM>::kDoubles;
+            const double* recA = reinterpret_cast<const double*>(grid_sm);
+            const double* recB = recA + (long long)L.NApad * R64;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const unsigned long long m = valid[s] ? ms[s] : mtile;
+                const Exact<DM> ex = exact_pair<DM>(p, s_pf, s_pd, k, m);
+                const double(&X)[DM] = ex.X;
+                const double(&Y)[DM] = ex.Y;
+                double bx = dist64<DM>(X, recA, d), by = dist64<DM>(Y, recB, d);
+                int ix = 0, iy = 0;
+                for (int j = 1; j < L.NA; ++j) {
+                    const double dj = dist64<DM>(X, recA + (long long)j * R64, d);
+                    if (dj < bx) {
+                        bx = dj;
+                        ix = j;
+                    }
+                }
+                for (int j = 1; j < L.NB; ++j) {
+                    const double dj = dist64<DM>(Y, recB + (long long)j * R64, d);
+                    if (dj < by) {
+                        by = dj;
+                        iy = j;
+                    }
+                }
+                ci[s] = ix;
+                cj[s] = iy;
+            }
+        }
+
+        // ---- counters p^k_ij (Sec. 3.3), per-sample cells, dumps
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (!valid[s]) continue;
+            const int i = ci[s], j = cj[s];
+            if ((unsigned)i >= (unsigned)L.NA || (unsigned)j >= (unsigned)L.NB) {
+                record_error(p.status, 6 /* QT_EDEVICE */, 2);
+                continue;
+            }
+            const long long e = (long long)i * L.NB + j;
+            if (L.hist_smem) atomicAdd(&hist[e], 1u);
+            else count_add(p.counts, p.counts_u32, L.coff + e, 1u);
+            if (p.cellsA) {
+                p.cellsA[ms[s]] = i;
+                p.cellsB[ms[s]] = j;
+            }
+            if (p.dump_count > 0 && (ms[s] % (unsigned long long)p.dump_stride) == 0ull) {
+                const unsigned long long t = ms[s] / (unsigned long long)p.dump_stride;
+                if (t < (unsigned long long)p.dump_count) {
+                    const long long row = (long long)k * p.dump_count + (long long)t;
+                    double zx[DM], zy[DM];
+                    exact_sample<DM>(p, s_pf, s_pd, k, ms[s], false, zx);
+                    exact_sample<DM>(p, s_pf, s_pd, k, ms[s], true, zy);
+                    for (int l = 0; l < d; ++l) {
+                        p.dumpX[row * d + l] = zx[l];
+                        p.dumpY[row * d + l] = zy[l];
+                    }
+                    p.dumpI[row] = i;
+                    p.dumpJ[row] = j;
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- final flush of the private histogram
+    if (hist_live) {
+        const int ent = s_L.NA * s_L.NB;
+        for (int e = tid; e < ent; e += blockDim.x) {
+            const uint32_t v = hist[e];
+            if (v) count_add(p.counts, p.counts_u32, s_L.coff + e, v);
+        }
+    }
+}
+
+}  // namespace qt

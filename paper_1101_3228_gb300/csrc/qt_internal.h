@@ -1,0 +1,87 @@
+// qt_internal.h -- structures shared by the host side of libqt and its kernels.
+#pragma once
+#include <cstdint>
+
+namespace qt {
+
+constexpr int kDMax = 16;          // largest state dimension
+constexpr int kChunk = 16;         // candidates per min-tracking chunk of the FP32 screen
+constexpr int kSlots = 2;          // ring slots of the streamed-grid mode
+
+enum Form : int32_t { kPlainF64 = 1, kF32Recheck = 2, kTcRecheck = 3, kRouterCert = 4 };
+enum Source : int32_t { kSampler = 0, kArrays = 1 };
+
+// Device status block, zeroed before every forward call.
+struct DevStatus {
+    int32_t code;                  // qt_status of the first error seen, 0 = none
+    int32_t where;                 // small tag of the failing site (diagnostics)
+    unsigned long long queue;      // persistent work-queue counter
+    unsigned long long rechecks;   // FP64 re-evaluations
+    unsigned long long candidates; // candidate distances (router form)
+    unsigned long long done_items; // work items finished
+    unsigned long long spare[3];
+};
+
+// One layer pair (k, k+1) of the forward step.
+struct LayerDesc {
+    int32_t NA, NB;                // grid sizes N_k, N_{k+1}
+    int32_t NApad, NBpad;          // sizes padded to a whole number of chunks
+    int32_t gridA, gridB;          // grid indices (k, k+1): index into the per-grid tables
+    int32_t segA, segB;            // streamed mode: segments per grid (0 = resident)
+    long long goffA, goffB;        // point offsets into the FP64 grids
+    long long roffA, roffB;        // record offsets (in records) into the prepared grids
+    long long coff;                // entry offset of the count block
+    long long item_begin;          // first work item of this layer
+    int32_t items;                 // work items (sample tiles) of this layer
+    int32_t hist_smem;             // 1 = shared-memory privatised histogram for this layer
+};
+
+// Per-grid tables written by the preparation kernel.
+struct GridInfo {
+    float mu[kDMax];               // centre (FP32) subtracted before the screen
+    float R;                       // max norm of the centred FP32 records (rounded up)
+    int32_t N, Npad;
+    long long goff, roff;
+};
+
+struct ForwardParams {
+    // problem
+    int32_t d, n;
+    int32_t form;                  // Form
+    int32_t source;                // Source
+    int32_t prec;                  // 0 = FP64 samples, 1 = FP32 samples
+    int32_t counts_u32;            // 1 = uint32 counts, 0 = int64
+    unsigned long long M;          // samples per layer
+    unsigned long long seed;
+    long long total_items;
+    int32_t tile;                  // samples per work item
+    int32_t rec_floats;            // floats per FP32 record (d+1 rounded up to 4)
+    int32_t rec64_doubles;         // doubles per FP64 record (d rounded up to 2)
+    int32_t smem_grid_bytes;       // bytes of dynamic smem reserved for grids
+    int32_t smem_hist_entries;     // u32 entries reserved for the private histogram
+    long long spin_budget;         // bounded waits; < 0: give up at once
+    // tables
+    const LayerDesc* layers;
+    const GridInfo* grids;
+    const float* params_f;         // [n][param_count(d)]
+    const double* params_d;        // [n][param_count(d)]
+    int32_t params_stride;
+    // data
+    const double* g64;             // FP64 grids [sum N][d] (exactness judge)
+    const float* rec32;            // FP32 records [sum Npad][rec_floats]
+    const double* rec64;           // FP64 records [sum Npad][rec64_doubles]
+    const double* srcX;            // Source::kArrays: samples [M][d]
+    const double* srcY;
+    void* counts;
+    int32_t* cellsA;               // Source::kArrays: optional per-sample cells
+    int32_t* cellsB;
+    // dump
+    long long dump_count, dump_stride;
+    double* dumpX;
+    double* dumpY;
+    int32_t* dumpI;
+    int32_t* dumpJ;
+    DevStatus* status;
+};
+
+}  // namespace qt

@@ -1,0 +1,24 @@
+// qt_launch.h -- dispatch from run-time (form, dimension class, samples per
+// thread) to the compiled instantiations of the forward kernel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "qt_internal.h"
+
+namespace qt {
+
+bool forward_variant_exists(int form, int dm, int S);
+
+// Launches one persistent grid (SM count x resident CTAs per SM).
+cudaError_t forward_launch(int form, int dm, int S, const ForwardParams& p, int block, int dyn_smem, int num_sms,
+                           int* blocks_per_sm, cudaStream_t st);
+
+// per-file dispatchers (qt_forward_*.cu)
+cudaError_t launch_f32_small(int dm, int S, const ForwardParams& p, int block, int dyn, int num_sms, int* bps,
+                             cudaStream_t st);
+cudaError_t launch_f32_large(int dm, int S, const ForwardParams& p, int block, int dyn, int num_sms, int* bps,
+                             cudaStream_t st);
+cudaError_t launch_f64(int dm, int S, const ForwardParams& p, int block, int dyn, int num_sms, int* bps,
+                       cudaStream_t st);
+
+}  // namespace qt
