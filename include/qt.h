@@ -219,6 +219,31 @@ QT_API qt_status qt_get_status(qt_ctx* ctx, void* stream, qt_stats* stats);
  * shape (descriptor tables, prepared grids, status words).                   */
 QT_API qt_status qt_transitions_workspace(const qt_model* model, const qt_options* opts, size_t* bytes);
 
+/* Allocation-free counting step, for callers that cannot allocate device
+ * memory (a host application whose allocator has reserved the device memory,
+ * a plug-in that may not own device memory, or a latency-bound loop that cannot
+ * afford the implicit synchronisation of cudaMalloc/cudaFree).  The paper has
+ * no counterpart: this is a packaging variant of qt_counts_from_samples.
+ *
+ * Same arguments and result as qt_counts_from_samples with the FP32 screen and
+ * FP64 recheck (counts OVERWRITTEN, cells optional), on the CURRENT device,
+ * without a context: the scratch (status and queue words, descriptors, a copy
+ * of both grids, their screened records) is a fixed array inside the library,
+ * one per device, kept until the process exits.  It calls no allocation
+ * routine.  The first call on a device looks up the array's device address;
+ * make that first call before any stream capture.  Every call reuses the same
+ * array, so calls that overlap on the GPU (two streams, two host threads)
+ * race: serialise them.  The call synchronises `stream` and returns the
+ * kernels' status.
+ * Limits: 1 <= d <= 16, NA + NB <= QT_NOALLOC_MAX_POINTS, and the screened
+ * records of both grids must fit one CTA's shared memory; otherwise QT_EINVAL
+ * is returned before any work is enqueued.                                    */
+#define QT_NOALLOC_MAX_POINTS 4096
+QT_API qt_status qt_counts_from_samples_noalloc(int32_t d, const double* gA, int64_t NA, const double* gB,
+                                                int64_t NB, const double* X, const double* Y, int64_t M,
+                                                int32_t counts_type, void* counts, int32_t* ii, int32_t* jj,
+                                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,7 @@ FORM_NAMES = {FORM_AUTO: "auto", FORM_PLAIN_F64: "plain_f64", FORM_F32_RECHECK: 
 # every symbol include/qt.h declares (checked by the CPU test of the ABI)
 EXPORTS = ["qt_create", "qt_destroy", "qt_last_error", "qt_status_string", "qt_default_options",
            "qt_build_grids", "qt_transitions", "qt_counts_from_samples", "qt_backward", "qt_price",
-           "qt_get_status", "qt_transitions_workspace"]
+           "qt_get_status", "qt_transitions_workspace", "qt_counts_from_samples_noalloc"]
 
 P = ctypes.c_void_p
 i32, i64, u32, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
@@ -74,6 +74,7 @@ _SIGS = {
     "qt_price": (i32, [P, P, P, i64, u64, P, P, P, P, P]),
     "qt_get_status": (i32, [P, P, P]),
     "qt_transitions_workspace": (i32, [P, P, P]),
+    "qt_counts_from_samples_noalloc": (i32, [i32, P, i64, P, i64, P, P, i64, i32, P, P, P, P]),
 }
 
 
