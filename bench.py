@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--M", type=int, default=0, help="override samples per layer")
+    ap.add_argument("--spt", type=int, default=0, help="samples per thread (0 = library choice)")
     return ap.parse_args()
 
 
@@ -241,7 +242,7 @@ def main():
     if form == B.FORM_AUTO:
         form = default_form(model, B)
     prec = model.prec
-    opts = B.options(form=form, prec=prec)
+    opts = B.options(form=form, prec=prec, samples_per_thread=args.spt)
     counts = torch.empty(int(np.sum(model.N[:-1] * model.N[1:])), dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # larger than the 129 MB L2
     units = model.n * model.M
