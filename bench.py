@@ -242,8 +242,11 @@ def main():
     if form == B.FORM_AUTO:
         form = default_form(model, B)
     prec = model.prec
-    opts = B.options(form=form, prec=prec, samples_per_thread=args.spt)
-    counts = torch.empty(int(np.sum(model.N[:-1] * model.N[1:])), dtype=torch.int64, device=dev)
+    entries = int(np.sum(model.N[:-1] * model.N[1:]))
+    # int64 counts unless they would take more than a quarter of the device (then uint32)
+    ctype = B.COUNTS_I64 if entries * 8 <= torch.cuda.get_device_properties(dev).total_memory // 4 else B.COUNTS_U32
+    opts = B.options(form=form, prec=prec, samples_per_thread=args.spt, counts_type=ctype)
+    counts = torch.empty(entries, dtype=torch.int64 if ctype == B.COUNTS_I64 else torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # larger than the 129 MB L2
     units = model.n * model.M
 
@@ -288,11 +291,13 @@ def main():
     plain = None
     pform = plain_form(model, B)
     if args.plain_steps > 0 and pform != form:
-        po = B.options(form=pform, prec=prec)
+        po = B.options(form=pform, prec=prec, counts_type=ctype)
         pms, _, _ = timed(po, args.plain_steps, 1)
         plain = {"form": B.FORM_NAMES[pform], "value": world * units / (pms / 1e3), "ms_per_step": pms}
 
     # end to end through the public API: host grids and payoff in, price out
+    del counts
+    torch.cuda.empty_cache()
     gh = grids.cpu().numpy()
     phi = W.payoff_values(model, gh)
     gpin = torch.from_numpy(gh).pin_memory()
@@ -338,6 +343,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": model.name, "d": model.d, "n": model.n, "N": int(model.N[-1]),
                            "M": model.M, "form": B.FORM_NAMES[form],
+                           "counts": "int64" if ctype == B.COUNTS_I64 else "uint32",
                            "sample_prec": "f32" if prec == 1 else "f64",
                            "l2": "256 MiB buffer written between timed steps",
                            "rechecks_per_step": rech},

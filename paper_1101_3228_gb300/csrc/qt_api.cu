@@ -71,6 +71,7 @@ struct qt_ctx {
     // autotuner cache: key -> samples per thread
     std::map<TuneKey, int> tune;
     int last_form = 0;
+    void* status_buf = nullptr;   // status block of the last forward call
 };
 
 namespace {
@@ -284,6 +285,8 @@ namespace {
 
 struct Plan {
     int form = 0, dm = 0, S = 0, block = 256;
+    bool streamed = false;
+    int seg_records = 0;
     int d = 0, n = 0, ngrids = 0;
     long long total_recs = 0;
     size_t grid_bytes = 0, hist_bytes = 0, dyn_smem = 0;
@@ -343,30 +346,36 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
     }
     P.total_recs = roff;
     const size_t rec_bytes = P.form == kF32Recheck ? (size_t)P.rec_floats * 4 : (size_t)P.rec64 * 8;
-    // samples per thread: tuned value if present, else a register-budget heuristic
-    int S = o->tile_samples_per_thread;
-    if (S <= 0) {
-        TuneKey key{P.form, P.dm, from_arrays ? 0 : o->sample_prec, 0};
-        auto it = ctx->tune.find(key);
-        S = it != ctx->tune.end() ? it->second : (P.form == kPlainF64 ? 2 : (P.dm <= 2 ? 8 : (P.dm <= 4 ? 4 : 2)));
-    }
-    if (!forward_variant_exists(P.form, P.dm, S))
-        return fail(ctx, QT_EUNSUPPORTED, "no kernel for form %d, d %d, %d samples per thread", form, d, S);
-    P.S = S;
-    P.block = 256;
-    P.tile = P.block * S;
-    // shared memory: both grids resident; the private histogram when it fits
+    // shared memory: both grids resident when they fit, else the streamed ring
     size_t budget = ctx->smem_optin > 24 * 1024 ? ctx->smem_optin - 24 * 1024 : 0;
     size_t gmax = 0;
     for (int k = 0; k < n; ++k) {
         const size_t b = (size_t)(P.grids[k].Npad + P.grids[k + 1].Npad) * rec_bytes;
         gmax = std::max(gmax, b);
     }
-    if (gmax > budget)
+    P.streamed = gmax > budget;
+    if (P.streamed && P.form != kF32Recheck)
         return fail(ctx, QT_EUNSUPPORTED,
-                    "grids of %zu bytes per layer pair exceed the %zu bytes of shared memory of the resident mode",
+                    "grids of %zu bytes per layer pair exceed the %zu bytes of shared memory of the plain FP64 form",
                     gmax, budget);
-    P.grid_bytes = round_up((long long)gmax, 128);
+    // samples per thread: tuned value if present, else a register-budget heuristic
+    int S = o->tile_samples_per_thread;
+    if (S <= 0) S = P.form == kPlainF64 ? 2 : (P.dm <= 2 ? 8 : (P.dm <= 4 ? 4 : 2));
+    if (!forward_variant_exists(P.form, P.dm, S, P.streamed))
+        return fail(ctx, QT_EUNSUPPORTED, "no kernel for form %d, d %d, %d samples per thread%s", form, d, S,
+                    P.streamed ? " (streamed grids)" : "");
+    P.S = S;
+    P.block = 256;
+    P.tile = P.block * S;
+    if (P.streamed) {
+        long long seg = (long long)(budget / (kSlots * rec_bytes)) / kChunk * kChunk;
+        seg = std::min<long long>(seg, 2048);
+        if (seg < kChunk) return fail(ctx, QT_EUNSUPPORTED, "records too large for the streamed ring");
+        P.seg_records = (int)seg;
+        P.grid_bytes = round_up((long long)(kSlots * seg * rec_bytes), 128);
+    } else {
+        P.grid_bytes = round_up((long long)gmax, 128);
+    }
     const bool force_smem = (o->flags & QT_FLAG_SMEM_HIST) != 0;
     const bool force_glob = (o->flags & QT_FLAG_GLOBAL_HIST) != 0;
     size_t hmax = 0;
@@ -394,7 +403,11 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
         // the layer to amortise the flush (or when forced)
         const long long ctas = (long long)ctx->num_sms * 2;
         const bool dense_enough = (M / std::max<long long>(ctas, 1)) >= 2 * (long long)L.NA * L.NB;
-        L.hist_smem = !force_glob && hb + P.grid_bytes <= budget && (force_smem || dense_enough);
+        L.hist_smem = !P.streamed && !force_glob && hb + P.grid_bytes <= budget && (force_smem || dense_enough);
+        if (P.streamed) {
+            L.segA = (int)((L.NApad + P.seg_records - 1) / P.seg_records);
+            L.segB = (int)((L.NBpad + P.seg_records - 1) / P.seg_records);
+        }
         if (L.hist_smem) hmax = std::max(hmax, hb);
         item += items_per_layer;
         coff += (long long)L.NA * L.NB;
@@ -404,6 +417,16 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
     P.hist_bytes = round_up((long long)hmax, 16);
     P.dyn_smem = P.grid_bytes + P.hist_bytes;
     return QT_OK;
+}
+
+bool stream_is_capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
 }
 
 // Enqueue the whole forward step on `st`: table uploads, zeroing, record
@@ -448,6 +471,7 @@ qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long
     fp.rec64_doubles = P.rec64;
     fp.smem_grid_bytes = (int)P.grid_bytes;
     fp.smem_hist_entries = (int)(P.hist_bytes / 4);
+    fp.seg_records = P.seg_records;
     fp.spin_budget = o->spin_budget == 0 ? (1ll << 26) : o->spin_budget;
     fp.layers = (const LayerDesc*)dlayers;
     fp.grids = (const GridInfo*)dgrids;
@@ -472,17 +496,21 @@ qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long
     }
     fp.status = dstatus;
     int blocks_per_sm = 0;
-    QT_CUDA(cudaEventRecord(ctx->ev_k0, st));
-    cudaError_t e = forward_launch(P.form, P.dm, P.S, fp, P.block, (int)P.dyn_smem, ctx->num_sms, &blocks_per_sm, st);
+    // timing events around the kernel; inside a capture they must be external
+    // event nodes to be recorded at every replay
+    const unsigned evflags = stream_is_capturing(st) ? cudaEventRecordExternal : cudaEventRecordDefault;
+    QT_CUDA(cudaEventRecordWithFlags(ctx->ev_k0, st, evflags));
+    cudaError_t e = forward_launch(P.form, P.dm, P.S, P.streamed, fp, P.block, (int)P.dyn_smem, ctx->num_sms,
+                                   &blocks_per_sm, st);
     if (e != cudaSuccess) return fail(ctx, QT_ECUDA, "forward kernel launch: %s", cudaGetErrorString(e));
-    QT_CUDA(cudaEventRecord(ctx->ev_k1, st));
+    QT_CUDA(cudaEventRecordWithFlags(ctx->ev_k1, st, evflags));
     ctx->timed = true;
     return QT_OK;
 }
 
 qt_status read_status(qt_ctx* ctx, cudaStream_t st, qt_stats* stats, long long samples, long long searches)
 {
-    void* dstatus = ctx->dev["status"].p;
+    void* dstatus = ctx->status_buf;
     DevStatus hs;
     memset(&hs, 0, sizeof hs);
     QT_CUDA(cudaStreamSynchronize(st));
@@ -504,50 +532,38 @@ qt_status read_status(qt_ctx* ctx, cudaStream_t st, qt_stats* stats, long long s
     return QT_OK;
 }
 
-bool stream_is_capturing(cudaStream_t st)
-{
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return cs != cudaStreamCaptureStatusNone;
-}
-
 void key_append(std::vector<unsigned char>& k, const void* p, size_t n)
 {
     const unsigned char* b = (const unsigned char*)p;
     k.insert(k.end(), b, b + n);
 }
 
-// Shared body of qt_transitions and qt_counts_from_samples.
-qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, const double* params_d_host,
-                         long long M, unsigned long long seed, const qt_options* o, int source, const FwdIO& io,
-                         qt_stats* stats, cudaStream_t st)
+// Upload the tables of plan P and run it on `st`, directly or through the
+// cached CUDA graph.  `tag` prefixes the workspace names (the autotuner keeps
+// its own buffers so that it never invalidates the cached graph).
+qt_status run_plan(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long M, unsigned long long seed,
+                   const qt_options* o, int source, const double* params_d_host, cudaStream_t st, bool use_graph,
+                   const std::string& tag)
 {
-    Plan P;
-    qt_status s = make_plan(ctx, d, n, Ns, mus, M, o, source == kArrays, P);
-    if (s) return s;
-    ctx->last_form = P.form == kPlainF64 ? QT_FORM_PLAIN_F64 : QT_FORM_F32_RECHECK;
-    // device workspace
+    qt_status s;
+    const int n = P.n;
     void *dlayers, *dgrids, *dpf, *dpd, *drec32 = nullptr, *drec64 = nullptr, *dstatus;
     const size_t pbytes = (size_t)std::max(1, n) * P.pstride;
-    if ((s = dev_get(ctx, "layers", sizeof(LayerDesc) * P.layers.size(), &dlayers))) return s;
-    if ((s = dev_get(ctx, "grids", sizeof(GridInfo) * P.grids.size(), &dgrids))) return s;
-    if ((s = dev_get(ctx, "params_f", pbytes * 4, &dpf))) return s;
-    if ((s = dev_get(ctx, "params_d", pbytes * 8, &dpd))) return s;
+    if ((s = dev_get(ctx, (tag + "layers").c_str(), sizeof(LayerDesc) * P.layers.size(), &dlayers))) return s;
+    if ((s = dev_get(ctx, (tag + "grids").c_str(), sizeof(GridInfo) * P.grids.size(), &dgrids))) return s;
+    if ((s = dev_get(ctx, (tag + "params_f").c_str(), pbytes * 4, &dpf))) return s;
+    if ((s = dev_get(ctx, (tag + "params_d").c_str(), pbytes * 8, &dpd))) return s;
     if (P.form == kF32Recheck) {
-        if ((s = dev_get(ctx, "rec32", (size_t)P.total_recs * P.rec_floats * 4, &drec32))) return s;
+        if ((s = dev_get(ctx, (tag + "rec32").c_str(), (size_t)P.total_recs * P.rec_floats * 4, &drec32))) return s;
     } else {
-        if ((s = dev_get(ctx, "rec64", (size_t)P.total_recs * P.rec64 * 8, &drec64))) return s;
+        if ((s = dev_get(ctx, (tag + "rec64").c_str(), (size_t)P.total_recs * P.rec64 * 8, &drec64))) return s;
     }
-    if ((s = dev_get(ctx, "status", sizeof(DevStatus), &dstatus))) return s;
-    // pinned host tables (kept alive for graph replays)
+    if ((s = dev_get(ctx, (tag + "status").c_str(), sizeof(DevStatus), &dstatus))) return s;
     void *hlayers, *hgrids, *hpf, *hpd;
-    if ((s = host_get(ctx, "layers", sizeof(LayerDesc) * P.layers.size(), &hlayers))) return s;
-    if ((s = host_get(ctx, "grids", sizeof(GridInfo) * P.grids.size(), &hgrids))) return s;
-    if ((s = host_get(ctx, "params_f", pbytes * 4, &hpf))) return s;
-    if ((s = host_get(ctx, "params_d", pbytes * 8, &hpd))) return s;
+    if ((s = host_get(ctx, (tag + "layers").c_str(), sizeof(LayerDesc) * P.layers.size(), &hlayers))) return s;
+    if ((s = host_get(ctx, (tag + "grids").c_str(), sizeof(GridInfo) * P.grids.size(), &hgrids))) return s;
+    if ((s = host_get(ctx, (tag + "params_f").c_str(), pbytes * 4, &hpf))) return s;
+    if ((s = host_get(ctx, (tag + "params_d").c_str(), pbytes * 8, &hpd))) return s;
     // the previous replay may still read the pinned tables
     QT_CUDA(cudaEventSynchronize(ctx->ev_tables));
     memcpy(hlayers, P.layers.data(), sizeof(LayerDesc) * P.layers.size());
@@ -562,26 +578,27 @@ qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
             pf[e] = (float)params_d_host[e];
         }
     }
-    // graph key: everything the enqueued work depends on
-    std::vector<unsigned char> key;
-    key_append(key, &P.form, sizeof P.form);
-    key_append(key, &P.S, sizeof P.S);
-    key_append(key, &M, sizeof M);
-    key_append(key, &seed, sizeof seed);
-    key_append(key, &source, sizeof source);
-    key_append(key, o, sizeof *o);
-    key_append(key, &io, sizeof io);
-    if (io.dump) key_append(key, io.dump, sizeof *io.dump);
-    key_append(key, P.layers.data(), sizeof(LayerDesc) * P.layers.size());
-    key_append(key, P.grids.data(), sizeof(GridInfo) * P.grids.size());
-    key_append(key, pd, pbytes * 8);
-
-    const bool direct = (o->flags & QT_FLAG_NO_GRAPH) || stream_is_capturing(st);
-    if (direct) {
+    ctx->status_buf = dstatus;
+    if (!use_graph) {
         s = enqueue_forward(ctx, P, io, M, seed, o, source, dpf, dpd, hpf, hpd, pbytes, dlayers, dgrids, hlayers,
                             hgrids, drec32, drec64, (DevStatus*)dstatus, st);
         if (s) return s;
     } else {
+        // graph key: everything the enqueued work depends on
+        std::vector<unsigned char> key;
+        key_append(key, &P.form, sizeof P.form);
+        key_append(key, &P.S, sizeof P.S);
+        key_append(key, &P.streamed, sizeof P.streamed);
+        key_append(key, &P.seg_records, sizeof P.seg_records);
+        key_append(key, &M, sizeof M);
+        key_append(key, &seed, sizeof seed);
+        key_append(key, &source, sizeof source);
+        key_append(key, o, sizeof *o);
+        key_append(key, &io, sizeof io);
+        if (io.dump) key_append(key, io.dump, sizeof *io.dump);
+        key_append(key, P.layers.data(), sizeof(LayerDesc) * P.layers.size());
+        key_append(key, P.grids.data(), sizeof(GridInfo) * P.grids.size());
+        key_append(key, pd, pbytes * 8);
         if (!ctx->gexec || key != ctx->gkey) {
             if (ctx->gexec) {
                 cudaGraphExecDestroy(ctx->gexec);
@@ -589,16 +606,15 @@ qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
             }
             cudaGraph_t graph = nullptr;
             QT_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t ce = cudaSuccess;
             qt_status es = enqueue_forward(ctx, P, io, M, seed, o, source, dpf, dpd, hpf, hpd, pbytes, dlayers,
                                            dgrids, hlayers, hgrids, drec32, drec64, (DevStatus*)dstatus,
                                            ctx->cap_stream);
             cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
-            if (es != QT_OK || ce != cudaSuccess || ee != cudaSuccess) {
+            if (es != QT_OK || ee != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
                 cudaGetLastError();
                 if (es != QT_OK) return es;
-                return fail(ctx, QT_ECUDA, "graph capture: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+                return fail(ctx, QT_ECUDA, "graph capture: %s", cudaGetErrorString(ee));
             }
             cudaError_t ie = cudaGraphInstantiate(&ctx->gexec, graph, 0);
             cudaGraphDestroy(graph);
@@ -611,6 +627,96 @@ qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
         QT_CUDA(cudaGraphLaunch(ctx->gexec, st));
     }
     QT_CUDA(cudaEventRecord(ctx->ev_tables, st));
+    return QT_OK;
+}
+
+// Autotuner: time every compiled samples-per-thread variant of this problem's
+// kernel class on a probe (first layers, bounded M) and keep the fastest for
+// the (form, mode, dimension class, precision, grid-size class) key.
+qt_status autotune(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, const double* params_d_host,
+                   long long M, unsigned long long seed, const qt_options* o, int source, const FwdIO& io,
+                   const Plan& base, const TuneKey& key, cudaStream_t st)
+{
+    static const int cands[] = {1, 2, 4, 8};
+    const int n2 = std::min(n, 2);
+    const long long M2 = std::min<long long>(M, base.dm <= 4 ? (1ll << 20) : (1ll << 16));
+    long long ent = 0;
+    for (int k = 0; k < n2; ++k) ent += Ns[k] * Ns[k + 1];
+    void* tcounts;
+    qt_status s = dev_get(ctx, "tune.counts", (size_t)ent * 8, &tcounts);
+    if (s) return s;
+    FwdIO tio = io;
+    tio.counts = tcounts;
+    tio.dump = nullptr;
+    tio.cellsA = tio.cellsB = nullptr;
+    cudaEvent_t e0, e1;
+    QT_CUDA(cudaEventCreate(&e0));
+    QT_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bestS = base.S;
+    for (int S : cands) {
+        if (!forward_variant_exists(base.form, base.dm, S, base.streamed)) continue;
+        qt_options to = *o;
+        to.tile_samples_per_thread = S;
+        to.counts_type = QT_COUNTS_I64;
+        to.flags |= QT_FLAG_NO_TUNE;
+        Plan P;
+        if (make_plan(ctx, d, n2, Ns, mus, M2, &to, source == kArrays, P) != QT_OK) continue;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            QT_CUDA(cudaEventRecord(e0, st));
+            if ((s = run_plan(ctx, P, tio, M2, seed, &to, source, params_d_host, st, false, "tune."))) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return s;
+            }
+            QT_CUDA(cudaEventRecord(e1, st));
+            QT_CUDA(cudaEventSynchronize(e1));
+            QT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        if (ms < best) {
+            best = ms;
+            bestS = S;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tune[key] = bestS;
+    return QT_OK;
+}
+
+TuneKey tune_key(const Plan& P, int prec, const int64_t* Ns, int n)
+{
+    long long mx = 1;
+    for (int k = 0; k <= n; ++k) mx = std::max<long long>(mx, Ns[k]);
+    int bucket = 0;
+    while ((1ll << bucket) < mx) ++bucket;
+    return TuneKey{P.form * 2 + (P.streamed ? 1 : 0), P.dm, prec, bucket};
+}
+
+// Shared body of qt_transitions and qt_counts_from_samples.
+qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, const double* params_d_host,
+                         long long M, unsigned long long seed, const qt_options* o, int source, const FwdIO& io,
+                         qt_stats* stats, cudaStream_t st)
+{
+    Plan P;
+    qt_status s = make_plan(ctx, d, n, Ns, mus, M, o, source == kArrays, P);
+    if (s) return s;
+    const bool capturing = stream_is_capturing(st);
+    if (o->tile_samples_per_thread <= 0 && !(o->flags & QT_FLAG_NO_TUNE) && !capturing && o->spin_budget >= 0) {
+        const TuneKey key = tune_key(P, source == kArrays ? 0 : o->sample_prec, Ns, n);
+        if (!ctx->tune.count(key)) {
+            if ((s = autotune(ctx, d, n, Ns, mus, params_d_host, M, seed, o, source, io, P, key, st))) return s;
+        }
+        qt_options to = *o;
+        to.tile_samples_per_thread = ctx->tune[key];
+        Plan P2;
+        if ((s = make_plan(ctx, d, n, Ns, mus, M, &to, source == kArrays, P2))) return s;
+        P = P2;
+    }
+    ctx->last_form = P.form == kPlainF64 ? QT_FORM_PLAIN_F64 : QT_FORM_F32_RECHECK;
+    const bool use_graph = !(o->flags & QT_FLAG_NO_GRAPH) && !capturing;
+    if ((s = run_plan(ctx, P, io, M, seed, o, source, params_d_host, st, use_graph, ""))) return s;
     if (stats) return read_status(ctx, st, stats, (long long)n * M, 2ll * n * M);
     return QT_OK;
 }

@@ -286,27 +286,118 @@ __device__ __noinline__ Exact<DM> exact_pair(const ForwardParams& p, const float
     return e;
 }
 
-// Scan `nchunk` chunks of records for S centred, scaled samples xs (xs = -2 x^).
+// Running minimum of the FP32 screen over one grid, per sample.
+template <int S>
+struct ScanState {
+    float B1[S];   // best score
+    float B2[S];   // smallest chunk minimum outside the best chunk
+    int bc[S];     // best chunk (global chunk index)
+};
+
+template <int S>
+__device__ __forceinline__ void scan_init(ScanState<S>& st)
+{
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        st.B1[s] = __int_as_float(0x7F800000);
+        st.B2[s] = __int_as_float(0x7F800000);
+        st.bc[s] = 0;
+    }
+}
+
+// Resolution of the best chunk, kept across segments in the streamed mode.
+template <int S>
+struct ResolveState {
+    float S1[S];   // smallest other score inside the best chunk
+    float r1[S];   // |g^| of the best record
+    int rc[S];     // chunk for which idx, S1, r1 hold (-1: none)
+    int idx[S];    // best record index
+};
+
+template <int S>
+__device__ __forceinline__ void resolve_init(ResolveState<S>& rs)
+{
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        rs.S1[s] = __int_as_float(0x7F800000);
+        rs.r1[s] = 0.0f;
+        rs.rc[s] = -1;
+        rs.idx[s] = -1;
+    }
+}
+
+// Re-score local chunk lc of `recs` (global chunk gc) for one sample: lowest
+// index achieving B1, smallest other score of the chunk, norm of the best record.
+template <int DM>
+__device__ __forceinline__ void resolve_chunk(const float* __restrict__ recs, int lc, int gc, const float (&x)[DM],
+                                              float B1, int& idx, float& S1, float& r1)
+{
+    constexpr int F = Rec32<DM>::kFloats;
+    idx = -1;
+    S1 = __int_as_float(0x7F800000);
+    r1 = 0.0f;
+    for (int q = 0; q < kChunk; ++q) {
+        const float* r = recs + (lc * kChunk + q) * F;
+        float sc = r[0];
+#pragma unroll
+        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], r[1 + l], sc);
+        if (sc == B1 && idx < 0) {
+            idx = gc * kChunk + q;
+            float n2 = 0.0f;
+#pragma unroll
+            for (int l = 0; l < DM; ++l) n2 = __fmaf_rn(r[1 + l], r[1 + l], n2);
+            r1 = __fsqrt_rn(n2);
+        } else {
+            S1 = fminf(S1, sc);
+        }
+    }
+}
+
+template <int DM>
+__device__ __forceinline__ void resolve_one(const float* __restrict__ recs, int bc, const float (&x)[DM], float B1,
+                                            int& idx, float& S1, float& r1)
+{
+    resolve_chunk<DM>(recs, bc, bc, x, B1, idx, S1, r1);
+}
+
+template <int V>
+__device__ __forceinline__ void load_pair(const float4* __restrict__ r4, int j, float4 (&a)[V], float4 (&b)[V])
+{
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        a[v] = r4[j * V + v];
+        b[v] = r4[(j + 1) * V + v];
+    }
+}
+
+// Scan `nchunk` chunks of records (global chunk index of the first: c0) for S
+// centred, scaled samples xs = -2 x^.  The next pair of records is loaded
+// while the current pair is scored.
 template <int DM, int S>
-__device__ __forceinline__ void screen_scan(const float* __restrict__ recs, int nchunk, const float (&xs)[S][DM],
-                                            float (&B1)[S], float (&B2)[S], int (&bc)[S])
+__device__ __forceinline__ void screen_scan(const float* __restrict__ recs, int nchunk, int c0,
+                                            const float (&xs)[S][DM], ScanState<S>& st)
 {
     constexpr int V = Rec32<DM>::kVec;
     const float4* r4 = reinterpret_cast<const float4*>(recs);
+    const int last = nchunk * kChunk - 2;
+    float4 na[V], nb[V];
+    load_pair<V>(r4, 0, na, nb);
     for (int c = 0; c < nchunk; ++c) {
         float mc[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) mc[s] = __int_as_float(0x7F800000);
-#pragma unroll 2
+#pragma unroll
         for (int q = 0; q < kChunk; q += 2) {
-            float ra[4 * V], rb[4 * V];
+            float4 ca[V], cb[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const float4 a = r4[(c * kChunk + q) * V + v];
-                const float4 b = r4[(c * kChunk + q + 1) * V + v];
-                ra[4 * v + 0] = a.x; ra[4 * v + 1] = a.y; ra[4 * v + 2] = a.z; ra[4 * v + 3] = a.w;
-                rb[4 * v + 0] = b.x; rb[4 * v + 1] = b.y; rb[4 * v + 2] = b.z; rb[4 * v + 3] = b.w;
+                ca[v] = na[v];
+                cb[v] = nb[v];
             }
+            const int jn = min(c * kChunk + q + 2, last);
+            load_pair<V>(r4, jn, na, nb);
+            const float* ra = reinterpret_cast<const float*>(ca);
+            const float* rb = reinterpret_cast<const float*>(cb);
 #pragma unroll
             for (int s = 0; s < S; ++s) {
                 float sa = ra[0], sb = rb[0];
@@ -320,40 +411,60 @@ __device__ __forceinline__ void screen_scan(const float* __restrict__ recs, int 
         }
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            B2[s] = fminf(B2[s], fmaxf(mc[s], B1[s]));
-            const bool nw = mc[s] < B1[s];
-            B1[s] = fminf(B1[s], mc[s]);
-            bc[s] = nw ? c : bc[s];
+            st.B2[s] = fminf(st.B2[s], fmaxf(mc[s], st.B1[s]));
+            const bool nw = mc[s] < st.B1[s];
+            st.B1[s] = fminf(st.B1[s], mc[s]);
+            st.bc[s] = nw ? c0 + c : st.bc[s];
         }
     }
 }
 
-// Re-score the best chunk of one sample: lowest index achieving B1 and the
-// smallest other score of that chunk.
-template <int DM>
-__device__ __forceinline__ void screen_resolve(const float* __restrict__ recs, int chunk, const float (&x)[DM],
-                                               float B1, int& idx, float& S1)
+// Streamed mode: for samples whose best chunk lies in the scanned records
+// [c0, c0 + nchunk) and is not resolved yet, resolve it while it is in
+// shared memory.
+template <int DM, int S>
+__device__ __forceinline__ void screen_resolve(const float* __restrict__ recs, int nchunk, int c0,
+                                               const float (&xs)[S][DM], const ScanState<S>& st,
+                                               ResolveState<S>& rs)
 {
-    constexpr int F = Rec32<DM>::kFloats;
-    idx = -1;
-    S1 = __int_as_float(0x7F800000);
-    for (int q = 0; q < kChunk; ++q) {
-        const float* r = recs + (chunk * kChunk + q) * F;
-        float sc = r[0];
 #pragma unroll
-        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], r[1 + l], sc);
-        if (sc == B1 && idx < 0) {
-            idx = chunk * kChunk + q;
-        } else {
-            S1 = fminf(S1, sc);
-        }
+    for (int s = 0; s < S; ++s) {
+        const int lc = st.bc[s] - c0;
+        if (st.bc[s] == rs.rc[s] || lc < 0 || lc >= nchunk) continue;
+        resolve_chunk<DM>(recs, lc, st.bc[s], xs[s], st.B1[s], rs.idx[s], rs.S1[s], rs.r1[s]);
+        rs.rc[s] = st.bc[s];
     }
+}
+
+// Certificate of the screened argmin (exact reasoning in the design notes):
+// with a = x - mu, g_j = c_j - mu, s_j = |g_j|^2 - 2 a.g_j the exact score and
+// s~_j the FP32 score, |s~_j - s_j| <= E(|g_j|), E(r) = (d+2) 2^-24 (r^2 + 2|a| r).
+// Every j with |g_j| > rho = |a| + sqrt(|a|^2 + s~_best + E(r_best)) has
+// s_j > s_best, and every other j has s_j >= s~_2nd - E(rho); so the screened
+// best is the exact FP64 argmin when s~_2nd - s~_best > E(rho) + E(r_best) + eta
+// (eta covers the FP64 rounding of the exact distance).  Slack factors absorb
+// the FP32 evaluation of this test.
+__device__ __forceinline__ bool screen_certified(int d, float A, float B1, float second, float r1n)
+{
+    const float Ap = A * (1.0f + 0x1p-18f);
+    const float cd = (float)(d + 2) * 0x1p-24f * (1.0f + 0x1p-10f);
+    const float r1 = r1n * (1.0f + 0x1p-18f);
+    const float E1 = cd * (r1 * r1 + 2.0f * Ap * r1);
+    const float U = B1 + E1;
+    const float A2 = Ap * Ap;
+    const float eta = 0x1p-44f * (A2 + fabsf(B1) + E1);
+    const float rad = fmaxf(A2 + U + 0x1p-18f * (A2 + fabsf(U)) + eta, 0.0f);
+    const float rho = Ap + __fsqrt_rn(rad);
+    const float Erho = cd * (rho * rho + 2.0f * Ap * rho);
+    const float thr = (Erho + E1 + eta) * (1.0f + 0x1p-16f);
+    return (second - B1) > thr;
 }
 
 // ------------------------------------------------------------------ the kernel
 
-template <int DM, int S, int FORM>
-__global__ void __launch_bounds__(256) forward_kernel(const ForwardParams p)
+// Small dimension classes keep two CTAs (16 warps) resident per SM.
+template <int DM, int S, int FORM, bool STREAMED>
+__global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) forward_kernel(const ForwardParams p)
 {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) unsigned long long s_bar;
@@ -363,6 +474,7 @@ __global__ void __launch_bounds__(256) forward_kernel(const ForwardParams p)
     __shared__ __align__(16) float s_pf[param_count(DM)];
     __shared__ __align__(16) double s_pd[param_count(DM)];
     __shared__ int s_abort;
+    __shared__ __align__(8) unsigned long long s_ring_bar[kSlots];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -373,6 +485,7 @@ __global__ void __launch_bounds__(256) forward_kernel(const ForwardParams p)
 
     if (tid == 0) {
         mbar_init(bar, 1);
+        for (int t = 0; t < kSlots; ++t) mbar_init(smem_u32(&s_ring_bar[t]), 1);
         fence_proxy_async();
         s_abort = 0;
     }
@@ -380,6 +493,9 @@ __global__ void __launch_bounds__(256) forward_kernel(const ForwardParams p)
 
     int cur = -1;
     uint32_t phase = 0;
+    uint32_t ring_phase[kSlots];
+#pragma unroll
+    for (int t = 0; t < kSlots; ++t) ring_phase[t] = 0;
     bool hist_live = false;
 
     while (true) {
@@ -424,8 +540,10 @@ __global__ void __launch_bounds__(256) forward_kernel(const ForwardParams p)
                 s_GB = p.grids[s_L.gridB];
             }
             __syncthreads();
-            // ---- stage both grids with bulk copies (TMA engine)
-            if (tid == 0) {
+            // ---- stage both grids with bulk copies (TMA engine); the streamed
+            // mode stages segments per tile instead
+            const bool resident = !STREAMED;
+            if (tid == 0 && resident) {
                 uint32_t bytesA, bytesB;
                 const void *srcA, *srcB;
                 if (FORM == kF32Recheck) {
@@ -458,7 +576,7 @@ __global__ void __launch_bounds__(256) forward_kernel(const ForwardParams p)
                 hist_live = true;
             }
             // ---- wait for the grids (bounded)
-            const bool ok = mbar_wait_bounded(bar, phase, p.spin_budget);
+            const bool ok = !resident || mbar_wait_bounded(bar, phase, p.spin_budget);
             if (!ok) {
                 // give up: record the timeout, let the copies land (bounded, fixed
                 // budget), then leave the kernel without touching the results
@@ -468,7 +586,7 @@ __global__ void __launch_bounds__(256) forward_kernel(const ForwardParams p)
                 }
                 mbar_wait_bounded(bar, phase, 1ll << 24);
             }
-            phase ^= 1u;
+            if (resident) phase ^= 1u;
             __syncthreads();
             if (s_abort) break;
             cur = k;
@@ -502,42 +620,132 @@ __global__ void __launch_bounds__(256) forward_kernel(const ForwardParams p)
                 Aa[s] = c.Aa;
                 Ab[s] = c.Ab;
             }
-            const float* recA = reinterpret_cast<const float*>(grid_sm);
-            const float* recB = recA + (long long)L.NApad * Rec32<DM>::kFloats;
             bool needA[S], needB[S];
+            if constexpr (!STREAMED) {
+                // ---- resident mode: both grids staged in shared memory at the layer switch
+                const float* recA = reinterpret_cast<const float*>(grid_sm);
+                const float* recB = recA + (long long)L.NApad * Rec32<DM>::kFloats;
 #pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                const float* rec = g == 0 ? recA : recB;
-                const int nch = (g == 0 ? L.NApad : L.NBpad) / kChunk;
-                const float R = g == 0 ? s_GA.R : s_GB.R;
-                float B1[S], B2[S];
-                int bc[S];
+                for (int g = 0; g < 2; ++g) {
+                    const float* rec = g == 0 ? recA : recB;
+                    const int nch = (g == 0 ? L.NApad : L.NBpad) / kChunk;
+                    ScanState<S> st;
+                    scan_init<S>(st);
+                    if (g == 0) screen_scan<DM, S>(rec, nch, 0, xa, st);
+                    else screen_scan<DM, S>(rec, nch, 0, yb, st);
 #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    B1[s] = __int_as_float(0x7F800000);
-                    B2[s] = __int_as_float(0x7F800000);
-                    bc[s] = 0;
-                }
-                if (g == 0) screen_scan<DM, S>(rec, nch, xa, B1, B2, bc);
-                else screen_scan<DM, S>(rec, nch, yb, B1, B2, bc);
-#pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    int idx;
-                    float S1;
-                    if (g == 0) screen_resolve<DM>(rec, bc[s], xa[s], B1[s], idx, S1);
-                    else screen_resolve<DM>(rec, bc[s], yb[s], B1[s], idx, S1);
-                    const float second = fminf(B2[s], S1);
-                    const float A = g == 0 ? Aa[s] : Ab[s];
-                    const float rr = R + A;
-                    const float thr = (float)(d + 2) * (rr * rr) * 0x1p-22f;
-                    const bool cert = (second - B1[s]) > thr && idx >= 0;
-                    if (g == 0) {
-                        ci[s] = idx;
-                        needA[s] = !cert && valid[s];
-                    } else {
-                        cj[s] = idx;
-                        needB[s] = !cert && valid[s];
+                    for (int s = 0; s < S; ++s) {
+                        int idx;
+                        float S1, r1;
+                        if (g == 0) resolve_one<DM>(rec, st.bc[s], xa[s], st.B1[s], idx, S1, r1);
+                        else resolve_one<DM>(rec, st.bc[s], yb[s], st.B1[s], idx, S1, r1);
+                        const float second = fminf(st.B2[s], S1);
+                        const bool cert =
+                            idx >= 0 && screen_certified(d, g == 0 ? Aa[s] : Ab[s], st.B1[s], second, r1);
+                        if (g == 0) {
+                            ci[s] = idx;
+                            needA[s] = !cert && valid[s];
+                        } else {
+                            cj[s] = idx;
+                            needB[s] = !cert && valid[s];
+                        }
                     }
+                }
+            } else {
+                // ---- streamed mode: segments of kSeg records through a two-slot
+                // ring of bulk copies; the CTA walks the segments in lockstep
+                const int seg_recs = p.seg_records;
+                const uint32_t seg_bytes = (uint32_t)seg_recs * Rec32<DM>::kFloats * 4u;
+                const int nA = L.segA, nB = L.segB, ntot = nA + nB;
+                auto seg_src = [&](int t, uint32_t& bytes) -> const float* {
+                    const bool isA = t < nA;
+                    const int ts = isA ? t : t - nA;
+                    const int npad = isA ? L.NApad : L.NBpad;
+                    const int first = ts * seg_recs;
+                    const int cnt = min(seg_recs, npad - first);
+                    bytes = (uint32_t)cnt * Rec32<DM>::kFloats * 4u;
+                    return p.rec32 + ((isA ? L.roffA : L.roffB) + first) * Rec32<DM>::kFloats;
+                };
+                bool pending[kSlots];   // a copy is in flight on this slot
+#pragma unroll
+                for (int t = 0; t < kSlots; ++t) pending[t] = t < ntot;
+                if (tid == 0) {
+                    fence_proxy_async();
+#pragma unroll
+                    for (int t = 0; t < kSlots; ++t) {
+                        if (t < ntot) {
+                            uint32_t bytes;
+                            const float* src = seg_src(t, bytes);
+                            const uint32_t sb = smem_u32(&s_ring_bar[t]);
+                            mbar_arrive_expect_tx(sb, bytes);
+                            bulk_g2s(smem_u32(grid_sm + t * seg_bytes), src, bytes, sb);
+                        }
+                    }
+                }
+                ScanState<S> st;
+                ResolveState<S> rs;
+                scan_init<S>(st);
+                resolve_init<S>(rs);
+                for (int t = 0; t < ntot; ++t) {
+                    const int slot = t % kSlots;
+                    const bool ok = mbar_wait_bounded(smem_u32(&s_ring_bar[slot]), ring_phase[slot], p.spin_budget);
+                    if (!ok && tid == 0) {
+                        record_error(p.status, 4 /* QT_ETIMEOUT */, 3);
+                        s_abort = 1;
+                    }
+                    if (!ok) mbar_wait_bounded(smem_u32(&s_ring_bar[slot]), ring_phase[slot], 1ll << 24);
+                    ring_phase[slot] ^= 1u;
+                    pending[slot] = false;
+                    const bool isA = t < nA;
+                    const int ts = isA ? t : t - nA;
+                    const int npad = isA ? L.NApad : L.NBpad;
+                    const int cnt = min(seg_recs, npad - ts * seg_recs);
+                    const float* rec = reinterpret_cast<const float*>(grid_sm + slot * seg_bytes);
+                    const int c0 = ts * seg_recs / kChunk;
+                    if (isA) {
+                        screen_scan<DM, S>(rec, cnt / kChunk, c0, xa, st);
+                        screen_resolve<DM, S>(rec, cnt / kChunk, c0, xa, st, rs);
+                    } else {
+                        screen_scan<DM, S>(rec, cnt / kChunk, c0, yb, st);
+                        screen_resolve<DM, S>(rec, cnt / kChunk, c0, yb, st, rs);
+                    }
+                    if (t == nA - 1 || t == ntot - 1) {
+#pragma unroll
+                        for (int s = 0; s < S; ++s) {
+                            const float second = fminf(st.B2[s], rs.S1[s]);
+                            const bool cert = rs.idx[s] >= 0 &&
+                                              screen_certified(d, isA ? Aa[s] : Ab[s], st.B1[s], second, rs.r1[s]);
+                            if (isA) {
+                                ci[s] = rs.idx[s];
+                                needA[s] = !cert && valid[s];
+                            } else {
+                                cj[s] = rs.idx[s];
+                                needB[s] = !cert && valid[s];
+                            }
+                        }
+                        scan_init<S>(st);
+                        resolve_init<S>(rs);
+                    }
+                    __syncthreads();   // every warp is done with this slot
+                    if (s_abort) break;
+                    if (t + kSlots < ntot) {
+                        pending[slot] = true;
+                        if (tid == 0) {
+                            uint32_t bytes;
+                            const float* src = seg_src(t + kSlots, bytes);
+                            const uint32_t sb = smem_u32(&s_ring_bar[slot]);
+                            fence_proxy_async();
+                            mbar_arrive_expect_tx(sb, bytes);
+                            bulk_g2s(smem_u32(grid_sm + slot * seg_bytes), src, bytes, sb);
+                        }
+                    }
+                }
+                if (s_abort) {
+                    // let the copies still in flight land before the CTA leaves
+#pragma unroll
+                    for (int t = 0; t < kSlots; ++t)
+                        if (pending[t]) mbar_wait_bounded(smem_u32(&s_ring_bar[t]), ring_phase[t], 1ll << 24);
+                    break;
                 }
             }
             // ---- exact FP64 recheck of uncertified searches, one warp per search

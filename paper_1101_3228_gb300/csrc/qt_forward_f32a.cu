@@ -5,7 +5,7 @@ cudaError_t launch_f32_small(int dm, int S, const ForwardParams& p, int block, i
                              cudaStream_t st)
 {
 #define QT_CASE(D, SS) \
-    if (dm == D && S == SS) return launch_forward<D, SS, kF32Recheck>(p, block, dyn, num_sms, bps, st);
+    if (dm == D && S == SS) return launch_forward<D, SS, kF32Recheck, false>(p, block, dyn, num_sms, bps, st);
     QT_CASE(1, 2) QT_CASE(1, 4) QT_CASE(1, 8)
     QT_CASE(2, 2) QT_CASE(2, 4) QT_CASE(2, 8)
     QT_CASE(3, 2) QT_CASE(3, 4) QT_CASE(3, 8)

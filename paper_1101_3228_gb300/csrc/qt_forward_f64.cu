@@ -6,7 +6,7 @@ cudaError_t launch_f64(int dm, int S, const ForwardParams& p, int block, int dyn
                        cudaStream_t st)
 {
 #define QT_CASE(D, SS) \
-    if (dm == D && S == SS) return launch_forward<D, SS, kPlainF64>(p, block, dyn, num_sms, bps, st);
+    if (dm == D && S == SS) return launch_forward<D, SS, kPlainF64, false>(p, block, dyn, num_sms, bps, st);
     QT_CASE(1, 1) QT_CASE(1, 2) QT_CASE(1, 4)
     QT_CASE(2, 1) QT_CASE(2, 2) QT_CASE(2, 4)
     QT_CASE(3, 1) QT_CASE(3, 2)
@@ -23,8 +23,11 @@ static bool in_list(int dm, int S, const int (*tab)[2], int n)
     return false;
 }
 
-bool forward_variant_exists(int form, int dm, int S)
+bool forward_variant_exists(int form, int dm, int S, bool streamed)
 {
+    static const int f32s[][2] = {{4, 1}, {4, 2}, {4, 4}, {6, 1}, {6, 2}, {6, 4}, {8, 1}, {8, 2}, {8, 4},
+                                  {10, 1}, {10, 2}, {10, 4}, {12, 1}, {12, 2}, {16, 1}, {16, 2}};
+    if (streamed) return form == kF32Recheck && in_list(dm, S, f32s, (int)(sizeof f32s / sizeof f32s[0]));
     static const int f32[][2] = {{1, 2}, {1, 4}, {1, 8}, {2, 2}, {2, 4}, {2, 8}, {3, 2}, {3, 4}, {3, 8},
                                  {4, 2}, {4, 4}, {4, 8}, {6, 1}, {6, 2}, {6, 4}, {8, 1}, {8, 2}, {8, 4},
                                  {10, 1}, {10, 2}, {10, 4}, {12, 1}, {12, 2}, {12, 4}, {16, 1}, {16, 2}};
@@ -35,9 +38,13 @@ bool forward_variant_exists(int form, int dm, int S)
     return false;
 }
 
-cudaError_t forward_launch(int form, int dm, int S, const ForwardParams& p, int block, int dyn_smem, int num_sms,
-                           int* blocks_per_sm, cudaStream_t st)
+cudaError_t forward_launch(int form, int dm, int S, bool streamed, const ForwardParams& p, int block, int dyn_smem,
+                           int num_sms, int* blocks_per_sm, cudaStream_t st)
 {
+    if (streamed) {
+        if (form != kF32Recheck) return cudaErrorInvalidValue;
+        return launch_f32_streamed(dm, S, p, block, dyn_smem, num_sms, blocks_per_sm, st);
+    }
     if (form == kPlainF64) return launch_f64(dm, S, p, block, dyn_smem, num_sms, blocks_per_sm, st);
     if (form == kF32Recheck) {
         if (dm <= 4) return launch_f32_small(dm, S, p, block, dyn_smem, num_sms, blocks_per_sm, st);

@@ -4,10 +4,10 @@
 
 namespace qt {
 
-template <int DM, int S, int FORM>
+template <int DM, int S, int FORM, bool STREAMED>
 cudaError_t launch_forward(const ForwardParams& p, int block, int dyn, int num_sms, int* bps, cudaStream_t st)
 {
-    auto kern = forward_kernel<DM, S, FORM>;
+    auto kern = forward_kernel<DM, S, FORM, STREAMED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
     int b = 0;

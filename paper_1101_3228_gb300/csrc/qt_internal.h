@@ -59,6 +59,7 @@ struct ForwardParams {
     int32_t rec64_doubles;         // doubles per FP64 record (d rounded up to 2)
     int32_t smem_grid_bytes;       // bytes of dynamic smem reserved for grids
     int32_t smem_hist_entries;     // u32 entries reserved for the private histogram
+    int32_t seg_records;           // streamed mode: records per ring slot (multiple of kChunk)
     long long spin_budget;         // bounded waits; < 0: give up at once
     // tables
     const LayerDesc* layers;

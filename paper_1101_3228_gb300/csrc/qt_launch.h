@@ -7,11 +7,11 @@
 
 namespace qt {
 
-bool forward_variant_exists(int form, int dm, int S);
+bool forward_variant_exists(int form, int dm, int S, bool streamed);
 
 // Launches one persistent grid (SM count x resident CTAs per SM).
-cudaError_t forward_launch(int form, int dm, int S, const ForwardParams& p, int block, int dyn_smem, int num_sms,
-                           int* blocks_per_sm, cudaStream_t st);
+cudaError_t forward_launch(int form, int dm, int S, bool streamed, const ForwardParams& p, int block, int dyn_smem,
+                           int num_sms, int* blocks_per_sm, cudaStream_t st);
 
 // per-file dispatchers (qt_forward_*.cu)
 cudaError_t launch_f32_small(int dm, int S, const ForwardParams& p, int block, int dyn, int num_sms, int* bps,
@@ -20,5 +20,7 @@ cudaError_t launch_f32_large(int dm, int S, const ForwardParams& p, int block, i
                              cudaStream_t st);
 cudaError_t launch_f64(int dm, int S, const ForwardParams& p, int block, int dyn, int num_sms, int* bps,
                        cudaStream_t st);
+cudaError_t launch_f32_streamed(int dm, int S, const ForwardParams& p, int block, int dyn, int num_sms, int* bps,
+                                cudaStream_t st);
 
 }  // namespace qt

@@ -109,7 +109,7 @@ extern "C" qt_status qt_counts_from_samples_noalloc(int32_t d, const double* gA,
     const long long NApad = up(NA, kChunk), NBpad = up(NB, kChunk);
     const size_t grid_bytes = (size_t)up((NApad + NBpad) * rec_floats * 4, 128);
     const size_t budget = prop.sharedMemPerBlockOptin > 24 * 1024 ? prop.sharedMemPerBlockOptin - 24 * 1024 : 0;
-    if (grid_bytes > budget || !forward_variant_exists(kF32Recheck, dm, S)) return QT_EINVAL;
+    if (grid_bytes > budget || !forward_variant_exists(kF32Recheck, dm, S, false)) return QT_EINVAL;
 
     DevStatus* dstatus = reinterpret_cast<DevStatus*>(base + kOffStatus);
     LayerDesc* dlayer = reinterpret_cast<LayerDesc*>(base + kOffLayer);
@@ -188,7 +188,7 @@ extern "C" qt_status qt_counts_from_samples_noalloc(int32_t d, const double* gA,
     fp.cellsB = jj;
     fp.status = dstatus;
     int bps = 0;
-    if (forward_launch(kF32Recheck, dm, S, fp, block, (int)grid_bytes, prop.multiProcessorCount, &bps, st) !=
+    if (forward_launch(kF32Recheck, dm, S, false, fp, block, (int)grid_bytes, prop.multiProcessorCount, &bps, st) !=
         cudaSuccess)
         return QT_ECUDA;
 

@@ -96,6 +96,38 @@ def test_counts_bit_exact(ctx, B, name, form, prec):
     assert _rel(V, Vref) <= 1e-12
 
 
+@pytest.mark.parametrize("name,N,M", [("ar8", 4000, 3001), ("maxcall10", 8000, 2003), ("basket4", 0, 5003)])
+def test_counts_bit_exact_large_grids(ctx, B, name, N, M):
+    """Grids too large for one CTA's shared memory: the streamed ring of bulk copies
+    (d = 8, N = 4000 and d = 10, N = 8000), and the widest uneven layers (N_k up to 2000)."""
+    if name == "basket4":
+        full = W.basket4(M=M)
+        keep = [0, full.n - 2, full.n - 1]
+        model = W.Model("basket4", full.d, 2, full.N[[0, full.n - 1, full.n]].copy(), full.A[keep[1:]],
+                        full.b[keep[1:]], full.T[keep[1:]], full.m[[0, full.n - 1, full.n]],
+                        full.L[[0, full.n - 1, full.n]], full.t[[0, full.n - 1, full.n]], full.r, full.payoff, full.K,
+                        full.weights, M, full.seed, full.prec, "kmeans")
+    else:
+        model = _model(name, M=M, n=2, N=N)
+    g = W.layer_grids(model, samples=3 * int(model.N[-1]), iters=3)
+    counts, stats, _ = ctx.transitions(model, _dev(g), model.M, model.seed, B.options(form=B.FORM_F32_RECHECK))
+    ref = oracle.transitions(model, g, model.M, model.seed, oracle.PREC_F32)
+    got = B.split_counts(model.N, counts.cpu().numpy())
+    for k in range(model.n):
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=f"layer {k}")
+    assert stats.device_status == 0
+
+
+def test_streamed_timeout_is_reported(ctx, B):
+    model = _model("ar8", M=600, n=2, N=4000)
+    g = _dev(W.layer_grids(model, samples=12000, iters=2))
+    with pytest.raises(B.QtError) as e:
+        ctx.transitions(model, g, model.M, model.seed, B.options(spin_budget=-1))
+    assert e.value.status == B.QT_ETIMEOUT
+    counts, _, _ = ctx.transitions(model, g, model.M, model.seed)
+    assert int(counts.sum()) == model.n * model.M
+
+
 def test_dump_samples_and_cells_bit_exact(ctx, B):
     """Every drawn (X_k, Y) and both cells, against the oracle's own sampler and search."""
     model = _model("ou2", M=5000, n=3, N=200)
