@@ -237,8 +237,8 @@ def main():
     seed = model.seed + 7919 * rank          # independent replica per rank
     grids = ctx.build_grids(model, grid_method(model), samples=max(20 * int(np.max(model.N)), 200000),
                             iters=20, seed=W.GRID_SEED_BASE + W.CONFIG_INDEX[model.name])
-    form = {"auto": B.FORM_AUTO, "plain_f64": B.FORM_PLAIN_F64, "f32_recheck": B.FORM_F32_RECHECK}.get(
-        args.form, B.FORM_AUTO)
+    form = {"auto": B.FORM_AUTO, "plain_f64": B.FORM_PLAIN_F64, "f32_recheck": B.FORM_F32_RECHECK,
+            "tc_recheck": B.FORM_TC_RECHECK}.get(args.form, B.FORM_AUTO)
     if form == B.FORM_AUTO:
         form = default_form(model, B)
     prec = model.prec

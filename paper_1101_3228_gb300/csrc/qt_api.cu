@@ -1,6 +1,7 @@
 // qt_api.cu -- host side of libqt: contexts, workspace, descriptor tables,
 // CUDA-graph capture of the forward step, the autotuner, and every C-ABI entry
 // point declared in include/qt.h.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +27,7 @@ __global__ void kmeans_assign_kernel(int, long long, const float*, int, const fl
                                      unsigned long long*, int);
 __global__ void kmeans_update_kernel(int, int, const unsigned long long*, const unsigned long long*, float*);
 __global__ void map_grid_kernel(int, int, const double*, const double*, const double*, double*);
+__global__ void prep_tc_tiles_kernel(const float*, GridInfo*, int, int, int, int, long long, __half*);
 }  // namespace qt
 
 using namespace qt;
@@ -287,6 +289,8 @@ struct Plan {
     int form = 0, dm = 0, S = 0, block = 256;
     bool streamed = false;
     int seg_records = 0;
+    int tc_k = 0, tc_slots = 0, tc_resident = 0;
+    long long tc_total_tiles = 0;
     int d = 0, n = 0, ngrids = 0;
     long long total_recs = 0;
     size_t grid_bytes = 0, hist_bytes = 0, dyn_smem = 0;
@@ -319,11 +323,15 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
     P.dm = dm_for(d);
     int form = o->form;
     if (form == QT_FORM_AUTO) form = QT_FORM_F32_RECHECK;
-    if (form == QT_FORM_TC_RECHECK || form == QT_FORM_ROUTER_CERT)
+    if (form == QT_FORM_ROUTER_CERT)
         return fail(ctx, QT_EUNSUPPORTED, "search form %d is not available in this build", form);
-    if (form != QT_FORM_PLAIN_F64 && form != QT_FORM_F32_RECHECK)
+    if (form != QT_FORM_PLAIN_F64 && form != QT_FORM_F32_RECHECK && form != QT_FORM_TC_RECHECK)
         return fail(ctx, QT_EINVAL, "unknown search form %d", form);
-    P.form = form == QT_FORM_PLAIN_F64 ? kPlainF64 : kF32Recheck;
+    P.form = form == QT_FORM_PLAIN_F64 ? kPlainF64 : (form == QT_FORM_TC_RECHECK ? kTcRecheck : kF32Recheck);
+    if (P.form == kTcRecheck) {
+        if (d > 10) return fail(ctx, QT_EUNSUPPORTED, "the tensor-core screen needs d <= 10 (3d + 2 <= 32 columns)");
+        P.dm = d <= 2 ? 2 : (d <= 4 ? 4 : (d <= 6 ? 6 : (d <= 8 ? 8 : 10)));
+    }
     if (!from_arrays && o->sample_prec != QT_PREC_F32 && o->sample_prec != QT_PREC_F64)
         return fail(ctx, QT_EINVAL, "sample_prec %d", o->sample_prec);
     P.rec_floats = rec_floats_for(P.dm);
@@ -338,13 +346,56 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
         for (int l = 0; l < d; ++l) G.mu[l] = (float)mus[(long long)g * d + l];
         G.R = 0.0f;
         G.N = (int)Ns[g];
-        G.Npad = P.form == kF32Recheck ? (int)round_up(Ns[g], kChunk) : (int)Ns[g];
+        G.Npad = P.form != kPlainF64 ? (int)round_up(Ns[g], kChunk) : (int)Ns[g];
         G.goff = goff;
         G.roff = roff;
+        G.tc_tiles = (int)((Ns[g] + kTcTileN - 1) / kTcTileN);
+        G.tc_toff = P.tc_total_tiles;
+        if (P.form == kTcRecheck) P.tc_total_tiles += G.tc_tiles;
         goff += Ns[g];
         roff += G.Npad;
     }
     P.total_recs = roff;
+    if (P.form == kTcRecheck) {
+        // one CTA of 128 threads per SM owns all 512 TMEM columns; operand tiles in a ring
+        P.tc_k = P.dm <= 4 ? 16 : 32;
+        const size_t tile_bytes = (size_t)kTcTileN * P.tc_k * 2;
+        P.tc_slots = (int)std::min<size_t>(16, (128 * 1024) / tile_bytes);
+        int tmax = 0;
+        for (int k = 0; k < n; ++k) tmax = std::max(tmax, P.grids[k].tc_tiles + P.grids[k + 1].tc_tiles);
+        P.tc_resident = tmax <= P.tc_slots;
+        P.S = 1;
+        P.block = 128;
+        P.tile = kTcTileM;
+        P.grid_bytes = 2 * (size_t)kTcTileM * P.tc_k * 2 + (size_t)P.tc_slots * tile_bytes;
+        P.hist_bytes = 0;
+        P.dyn_smem = P.grid_bytes;
+        P.layers.resize(n);
+        long long item = 0, coff = 0;
+        const long long items_per_layer = (M + P.tile - 1) / P.tile;
+        for (int k = 0; k < n; ++k) {
+            LayerDesc& L = P.layers[k];
+            memset(&L, 0, sizeof L);
+            L.NA = (int)Ns[k];
+            L.NB = (int)Ns[k + 1];
+            L.NApad = P.grids[k].Npad;
+            L.NBpad = P.grids[k + 1].Npad;
+            L.gridA = k;
+            L.gridB = k + 1;
+            L.goffA = P.grids[k].goff;
+            L.goffB = P.grids[k + 1].goff;
+            L.roffA = P.grids[k].roff;
+            L.roffB = P.grids[k + 1].roff;
+            L.coff = coff;
+            L.item_begin = item;
+            L.items = (int)items_per_layer;
+            item += items_per_layer;
+            coff += (long long)L.NA * L.NB;
+        }
+        P.total_items = item;
+        P.count_entries = coff;
+        return QT_OK;
+    }
     const size_t rec_bytes = P.form == kF32Recheck ? (size_t)P.rec_floats * 4 : (size_t)P.rec64 * 8;
     // shared memory: both grids resident when they fit, else the streamed ring
     size_t budget = ctx->smem_optin > 24 * 1024 ? ctx->smem_optin - 24 * 1024 : 0;
@@ -452,11 +503,24 @@ qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long
         const long long nb = (P.total_recs + blk - 1) / blk;
         prep_records_kernel<<<(unsigned)nb, blk, 0, st>>>(
             io.g64, (GridInfo*)dgrids, P.ngrids, P.d, P.rec_floats, P.rec64, P.total_recs,
-            P.form == kF32Recheck ? (float*)drec32 : nullptr, P.form == kPlainF64 ? (double*)drec64 : nullptr);
+            P.form != kPlainF64 ? (float*)drec32 : nullptr, P.form == kPlainF64 ? (double*)drec64 : nullptr);
+        QT_CUDA(cudaGetLastError());
+    }
+    void* dtiles = nullptr;
+    if (P.form == kTcRecheck) {
+        qt_status ts = dev_get(ctx, "tctiles", (size_t)P.tc_total_tiles * kTcTileN * P.tc_k * 2, &dtiles);
+        if (ts) return ts;
+        const long long rows = P.tc_total_tiles * kTcTileN;
+        prep_tc_tiles_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(
+            (const float*)drec32, (GridInfo*)dgrids, P.ngrids, P.d, P.rec_floats, P.tc_k, rows, (__half*)dtiles);
         QT_CUDA(cudaGetLastError());
     }
     ForwardParams fp;
     memset(&fp, 0, sizeof fp);
+    fp.tc_tiles = dtiles;
+    fp.tc_k = P.tc_k;
+    fp.tc_slots = P.tc_slots;
+    fp.tc_resident = P.tc_resident;
     fp.d = P.d;
     fp.n = P.n;
     fp.form = P.form;
@@ -553,7 +617,7 @@ qt_status run_plan(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long M, uns
     if ((s = dev_get(ctx, (tag + "grids").c_str(), sizeof(GridInfo) * P.grids.size(), &dgrids))) return s;
     if ((s = dev_get(ctx, (tag + "params_f").c_str(), pbytes * 4, &dpf))) return s;
     if ((s = dev_get(ctx, (tag + "params_d").c_str(), pbytes * 8, &dpd))) return s;
-    if (P.form == kF32Recheck) {
+    if (P.form != kPlainF64) {
         if ((s = dev_get(ctx, (tag + "rec32").c_str(), (size_t)P.total_recs * P.rec_floats * 4, &drec32))) return s;
     } else {
         if ((s = dev_get(ctx, (tag + "rec64").c_str(), (size_t)P.total_recs * P.rec64 * 8, &drec64))) return s;
@@ -638,7 +702,14 @@ qt_status autotune(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* m
                    const Plan& base, const TuneKey& key, cudaStream_t st)
 {
     static const int cands[] = {1, 2, 4, 8};
-    const int n2 = std::min(n, 2);
+    // probe the widest pair of layers (the costliest work items)
+    int k0 = 0;
+    for (int k = 1; k < n; ++k)
+        if (Ns[k] + Ns[k + 1] > Ns[k0] + Ns[k0 + 1]) k0 = k;
+    const int n2 = std::min(n - k0, 2);
+    Ns += k0;
+    mus += (long long)k0 * d;
+    if (params_d_host) params_d_host += (long long)k0 * base.pstride;
     const long long M2 = std::min<long long>(M, base.dm <= 4 ? (1ll << 20) : (1ll << 16));
     long long ent = 0;
     for (int k = 0; k < n2; ++k) ent += Ns[k] * Ns[k + 1];
@@ -703,7 +774,8 @@ qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
     qt_status s = make_plan(ctx, d, n, Ns, mus, M, o, source == kArrays, P);
     if (s) return s;
     const bool capturing = stream_is_capturing(st);
-    if (o->tile_samples_per_thread <= 0 && !(o->flags & QT_FLAG_NO_TUNE) && !capturing && o->spin_budget >= 0) {
+    if (P.form != kTcRecheck && o->tile_samples_per_thread <= 0 && !(o->flags & QT_FLAG_NO_TUNE) && !capturing &&
+        o->spin_budget >= 0) {
         const TuneKey key = tune_key(P, source == kArrays ? 0 : o->sample_prec, Ns, n);
         if (!ctx->tune.count(key)) {
             if ((s = autotune(ctx, d, n, Ns, mus, params_d_host, M, seed, o, source, io, P, key, st))) return s;
@@ -714,7 +786,8 @@ qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
         if ((s = make_plan(ctx, d, n, Ns, mus, M, &to, source == kArrays, P2))) return s;
         P = P2;
     }
-    ctx->last_form = P.form == kPlainF64 ? QT_FORM_PLAIN_F64 : QT_FORM_F32_RECHECK;
+    ctx->last_form = P.form == kPlainF64 ? QT_FORM_PLAIN_F64
+                                         : (P.form == kTcRecheck ? QT_FORM_TC_RECHECK : QT_FORM_F32_RECHECK);
     const bool use_graph = !(o->flags & QT_FLAG_NO_GRAPH) && !capturing;
     if ((s = run_plan(ctx, P, io, M, seed, o, source, params_d_host, st, use_graph, ""))) return s;
     if (stats) return read_status(ctx, st, stats, (long long)n * M, 2ll * n * M);

@@ -1,0 +1,599 @@
+// qt_forward_tc.cu -- the forward step of Algorithm III (Pages & Wilbertz,
+// arXiv:1101.3228, Sec. 4) with the nearest-cell screen on the 5th-generation
+// tensor cores (tcgen05.mma, accumulators in tensor memory).
+//
+// The screen scores s_j = |g_j|^2 - 2 x^.g_j (g_j, x^ centred on the grid's
+// FP32 centre) are one GEMM per 128 samples x 256 grid points: sample rows
+// [a_hi, a_hi, a_lo, 1, 1] times grid rows [g_hi, g_lo, g_hi, cc_hi, cc_lo],
+// a = -2 sigma x^, g = sigma g^, cc = sigma^2 |g^|^2, each split into an FP16
+// head and an FP16 tail, sigma = 2^tc_exp so that the grid fits in [-1, 1].
+// The three cross products reproduce the FP32 score to about 2^-21 relative
+// (the tail x tail product is below 2^-22); K = 16 holds 3d + 2 columns for
+// d <= 4, K = 32 for d <= 10.
+//
+// Per work item (layer k, 128 samples): one thread per sample draws the pair,
+// writes both sample rows into shared memory, and the CTA walks the operand
+// tiles of Gamma_k and Gamma_{k+1}: thread 0 issues the MMA of tile t + 1 into
+// one of two 256-column TMEM accumulators while all 128 threads read tile t
+// with tcgen05.ld and keep, per sample, the running minimum per 16-column chunk
+// (best, smallest other chunk minimum, best chunk).  Operand tiles arrive by
+// bulk copies (TMA engine); they stay in shared memory for the whole layer when
+// both grids fit, else they stream through a ring.
+//
+// Exactness: the best chunk is re-scored on the CUDA cores in FP32 (index and
+// second score inside the chunk), and the pick is certified against the exact
+// FP64 distance with the FP32 bound inside the chunk and the tensor-core bound
+// outside it; uncertified samples get a warp-wide FP32 re-screen of the whole
+// grid and, if that cannot certify either, the exact FP64 search.
+#include <cuda_fp16.h>
+
+#include "qt_forward.cuh"
+#include "qt_launch.h"
+
+namespace qt {
+
+namespace {
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    // tcgen05 shared-memory matrix descriptor, canonical K-major layout, no swizzle
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float min16(const float* v)
+{
+    const float a = min3f(v[0], v[1], v[2]);
+    const float b = min3f(v[3], v[4], v[5]);
+    const float c = min3f(v[6], v[7], v[8]);
+    const float e = min3f(v[9], v[10], v[11]);
+    const float f = min3f(v[12], v[13], v[14]);
+    return min3f(min3f(a, b, c), min3f(e, f, v[15]), __int_as_float(0x7F800000));
+}
+
+// Bound on |tensor-core score - exact score| in FP32-score units for a grid
+// point at distance r from the centre (A = |x^|): the FP32 bound (d+2) 2^-24
+// plus 32 FP32 additions of the MMA (2^-23 each, counted as truncations), the
+// dropped tail product and the head/tail representation (3 * 2^-22), and the
+// absolute floor of the FP16 tails (2^-25 each) divided by sigma^2.
+__device__ __forceinline__ float tc_bound(int d, float A, float r, float inv_sigma)
+{
+    const float rel = 1.5f * 0x1p-18f;
+    const float absf = (0x1p-23f * sqrtf((float)d) * (A + r) * (1.0f / inv_sigma) + 0x1p-24f) * inv_sigma * inv_sigma;
+    return rel * (r * r + 2.0f * A * r) + absf;
+}
+
+__device__ __forceinline__ float cc_bound(int d, float A, float r)
+{
+    return (float)(d + 2) * 0x1p-24f * (1.0f + 0x1p-10f) * (r * r + 2.0f * A * r);
+}
+
+// FP32 scores of one 16-record chunk of a grid (records in global memory):
+// lowest-index minimum, the smallest other score, the norm of the best record.
+template <int DM>
+__device__ __forceinline__ void cc_chunk(const float* __restrict__ recs, int chunk, const float (&x)[DM], int& idx,
+                                         float& best, float& S1, float& r1)
+{
+    constexpr int F = Rec32<DM>::kFloats;
+    idx = -1;
+    best = __int_as_float(0x7F800000);
+    S1 = __int_as_float(0x7F800000);
+    int bq = 0;
+    for (int q = 0; q < kChunk; ++q) {
+        const float* r = recs + (chunk * kChunk + q) * F;
+        float sc = r[0];
+#pragma unroll
+        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], r[1 + l], sc);
+        if (sc < best) {
+            S1 = fminf(S1, best);
+            best = sc;
+            bq = q;
+        } else {
+            S1 = fminf(S1, sc);
+        }
+    }
+    idx = chunk * kChunk + bq;
+    const float* r = recs + idx * F;
+    float n2 = 0.0f;
+#pragma unroll
+    for (int l = 0; l < DM; ++l) n2 = __fmaf_rn(r[1 + l], r[1 + l], n2);
+    r1 = __fsqrt_rn(n2);
+}
+
+// Mixed certificate: FP32 scores inside the best chunk, tensor-core scores
+// (B2tc: smallest chunk minimum outside it, FP32-score units) outside.
+__device__ __forceinline__ bool tc_certified(int d, float A, float best, float S1, float B2tc, float r1,
+                                             float inv_sigma)
+{
+    const float Ap = A * (1.0f + 0x1p-18f);
+    const float r1p = r1 * (1.0f + 0x1p-18f);
+    const float E1 = cc_bound(d, Ap, r1p);
+    const float U = best + E1;
+    const float A2 = Ap * Ap;
+    const float eta = 0x1p-44f * (A2 + fabsf(best) + E1);
+    const float rad = fmaxf(A2 + U + 0x1p-18f * (A2 + fabsf(U)) + eta, 0.0f);
+    const float rho = Ap + __fsqrt_rn(rad);
+    const float lo_in = S1 - cc_bound(d, Ap, rho);
+    const float lo_out = B2tc - tc_bound(d, Ap, rho, inv_sigma);
+    const float lhs = fminf(lo_in, lo_out), rhs = U + eta;
+    // additive slack for the FP32 evaluation of both sides
+    return lhs - rhs > 0x1p-20f * (fabsf(lhs) + fabsf(rhs)) + eta;
+}
+
+// Whole-warp FP32 re-screen of one lane's sample over a grid (records in global
+// memory); returns the certified cell or -1.
+template <int DM>
+__device__ __noinline__ int warp_screen_nn(const float (&xs)[DM], float A, int src, const float* __restrict__ recs,
+                                           int Npad, int d)
+{
+    constexpr int F = Rec32<DM>::kFloats;
+    float x[DM];
+#pragma unroll
+    for (int l = 0; l < DM; ++l) x[l] = __shfl_sync(0xFFFFFFFFu, xs[l], src);
+    const float Av = __shfl_sync(0xFFFFFFFFu, A, src);
+    const int lane = threadIdx.x & 31;
+    float b1 = __int_as_float(0x7F800000), b2 = __int_as_float(0x7F800000);
+    int i1 = 0x7FFFFFFF;
+    for (int j = lane; j < Npad; j += 32) {
+        const float* r = recs + j * F;
+        float sc = r[0];
+#pragma unroll
+        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], r[1 + l], sc);
+        if (sc < b1) {
+            b2 = b1;
+            b1 = sc;
+            i1 = j;
+        } else {
+            b2 = fminf(b2, sc);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const float ob1 = __shfl_xor_sync(0xFFFFFFFFu, b1, off);
+        const float ob2 = __shfl_xor_sync(0xFFFFFFFFu, b2, off);
+        const int oi = __shfl_xor_sync(0xFFFFFFFFu, i1, off);
+        if (ob1 < b1 || (ob1 == b1 && oi < i1)) {
+            b2 = fminf(ob2, b1);
+            b1 = ob1;
+            i1 = oi;
+        } else {
+            b2 = fminf(b2, ob1);
+        }
+    }
+    const float* r = recs + i1 * F;
+    float n2 = 0.0f;
+#pragma unroll
+    for (int l = 0; l < DM; ++l) n2 = __fmaf_rn(r[1 + l], r[1 + l], n2);
+    return screen_certified(d, Av, b1, b2, __fsqrt_rn(n2)) ? i1 : -1;
+}
+
+}  // namespace
+
+// FP16 operand tiles of every grid: row j of grid g (tile j/256) holds
+// [g_hi (d), g_lo (d), g_hi (d), cc_hi, cc_lo, 0 ...] of sigma g^ and
+// sigma^2 cc; padded rows carry cc_hi = +inf.  Layout inside a tile: core
+// matrices of 8 rows x 8 halves, (row block, K block) at ((n/8)(K/8) + k/8) * 64.
+__global__ void prep_tc_tiles_kernel(const float* __restrict__ rec32, GridInfo* gi, int ngrids, int d,
+                                     int rec_floats, int K, long long total_rows, __half* tiles)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= total_rows) return;
+    int lo = 0, hi = ngrids - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (gi[mid].tc_toff * kTcTileN <= r) lo = mid; else hi = mid - 1;
+    }
+    const GridInfo& G = gi[lo];
+    const long long j = r - G.tc_toff * kTcTileN;
+    // sigma = 2^e with sigma R <= 1
+    int e = 0;
+    if (G.R > 0.0f) {
+        int ex;
+        frexpf(G.R, &ex);   // R = f 2^ex, f in [0.5, 1)
+        e = -ex;
+    }
+    if (j == 0) gi[lo].tc_exp = e;
+    const float sg = ldexpf(1.0f, e);
+    const long long tile = G.tc_toff + j / kTcTileN;
+    const int n = (int)(j % kTcTileN);
+    __half* t = tiles + tile * (long long)kTcTileN * K;
+    auto put = [&](int k, __half v) { t[((n >> 3) * (K >> 3) + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7)] = v; };
+    for (int k = 0; k < K; ++k) put(k, __float2half_rn(0.0f));
+    if (j < G.N) {
+        const float* rc = rec32 + (G.roff + j) * rec_floats;
+        for (int l = 0; l < d; ++l) {
+            const float v = sg * rc[1 + l];
+            const __half h = __float2half_rn(v);
+            const __half lo16 = __float2half_rn(v - __half2float(h));
+            put(l, h);
+            put(d + l, lo16);
+            put(2 * d + l, h);
+        }
+        const float c = sg * sg * rc[0];
+        const __half ch = __float2half_rn(c);
+        put(3 * d, ch);
+        put(3 * d + 1, __float2half_rn(c - __half2float(ch)));
+    } else {
+        put(3 * d, __float2half_rn(__int_as_float(0x7F800000)));
+    }
+}
+
+template <int DM, int KT>
+__global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams p)
+{
+    constexpr int K = 16 * KT;
+    constexpr int kTileBytes = kTcTileN * K * 2;
+    constexpr int kAbytes = kTcTileM * K * 2;
+    extern __shared__ __align__(128) unsigned char dsm_tc[];
+    __shared__ __align__(8) unsigned long long s_bfull[16];
+    __shared__ __align__(8) unsigned long long s_mma[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ long long s_item;
+    __shared__ LayerDesc s_L;
+    __shared__ GridInfo s_GA, s_GB;
+    __shared__ __align__(16) float s_pf[param_count(DM)];
+    __shared__ __align__(16) double s_pd[param_count(DM)];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int d = p.d;
+    const int RS = p.tc_slots;
+    unsigned char* sA = dsm_tc;                     // two sample operands (grid A, grid B)
+    unsigned char* sB = dsm_tc + 2 * kAbytes;         // operand tile ring
+    const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
+
+    if (tid == 0) {
+        for (int t = 0; t < RS; ++t) mbar_init(smem_u32(&s_bfull[t]), 1);
+        mbar_init(smem_u32(&s_mma[0]), 1);
+        mbar_init(smem_u32(&s_mma[1]), 1);
+        fence_proxy_async();
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    uint32_t bphase = 0;                   // bit t: parity of slot t's barrier
+    uint32_t mphase = 0;                   // bit b: parity of accumulator b's barrier
+    uint32_t idesc = (1u << 4) | ((uint32_t)(kTcTileN >> 3) << 17) | ((uint32_t)(kTcTileM >> 4) << 24);
+    int cur = -1;
+
+    while (true) {
+        if (tid == 0) {
+            long long it = -1;
+            if (*((volatile int32_t*)&p.status->code) == 0) it = (long long)atomicAdd(&p.status->queue, 1ull);
+            s_item = it;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item < 0 || item >= p.total_items) break;
+        int k = (cur >= 0 && item >= s_L.item_begin && item < s_L.item_begin + s_L.items) ? cur : -1;
+        if (k < 0) {
+            int lo = 0, hi = p.n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (p.layers[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+            }
+            k = lo;
+        }
+        const bool new_layer = k != cur;
+        if (new_layer) {
+            __syncthreads();
+            if (tid == 0) {
+                s_L = p.layers[k];
+                s_GA = p.grids[s_L.gridA];
+                s_GB = p.grids[s_L.gridB];
+            }
+            if (p.source == kSampler) {
+                const int pc = param_count(d);
+                for (int e = tid; e < pc; e += blockDim.x) {
+                    s_pf[e] = p.params_f[(long long)k * p.params_stride + e];
+                    s_pd[e] = p.params_d[(long long)k * p.params_stride + e];
+                }
+            }
+            __syncthreads();
+            cur = k;
+        }
+        const LayerDesc& L = s_L;
+        const int tA = s_GA.tc_tiles, tB = s_GB.tc_tiles, nT = tA + tB;
+        const bool resident = p.tc_resident != 0;
+        auto tile_src = [&](int i) -> const unsigned char* {
+            const long long gt = i < tA ? s_GA.tc_toff + i : s_GB.tc_toff + (i - tA);
+            return reinterpret_cast<const unsigned char*>(p.tc_tiles) + gt * (long long)kTileBytes;
+        };
+        // ---- operand tiles: all of them once per layer (resident) or the first RS (streamed)
+        if (tid == 0 && (!resident || new_layer)) {
+            fence_proxy_async();
+            const int first = resident ? nT : min(RS, nT);
+            for (int i = 0; i < first; ++i) {
+                const uint32_t b = smem_u32(&s_bfull[i]);
+                mbar_arrive_expect_tx(b, kTileBytes);
+                bulk_g2s(sB_u + i * kTileBytes, tile_src(i), kTileBytes, b);
+            }
+        }
+        bool loaded_now = !resident || new_layer;    // barriers of this item's tiles still to be waited
+
+        // ---- one sample per thread: draw, centre, write both operand rows
+        const unsigned long long mtile = (unsigned long long)(item - L.item_begin) * kTcTileM;
+        const unsigned long long ms = mtile + (unsigned long long)tid;
+        const bool valid = ms < p.M;
+        const Centred<DM> cs = centred_sample<DM>(p, s_pf, s_pd, s_GA.mu, s_GB.mu, k, valid ? ms : mtile);
+        bool bigA = false, bigB = false;   // outside the FP16 range: skip the screen, search exactly
+        {
+            const float sgA = ldexpf(1.0f, s_GA.tc_exp), sgB = ldexpf(1.0f, s_GB.tc_exp);
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                __half row[K];
+#pragma unroll
+                for (int q = 0; q < K; ++q) row[q] = __float2half_rn(0.0f);
+                bool big = false;
+#pragma unroll
+                for (int l = 0; l < DM; ++l) {
+                    const float v = (g == 0 ? sgA * cs.xa[l] : sgB * cs.yb[l]);
+                    big = big || !(fabsf(v) <= 16384.0f);
+                }
+#pragma unroll
+                for (int l = 0; l < DM; ++l) {
+                    const float v = big ? 0.0f : (g == 0 ? sgA * cs.xa[l] : sgB * cs.yb[l]);
+                    const __half h = __float2half_rn(v);
+                    if (l < d) {
+                        row[l] = h;
+                        row[d + l] = h;
+                        row[2 * d + l] = __float2half_rn(v - __half2float(h));
+                    }
+                }
+                if (g == 0) bigA = big; else bigB = big;
+                row[3 * d] = __float2half_rn(1.0f);
+                row[3 * d + 1] = __float2half_rn(1.0f);
+                unsigned char* base = sA + g * kAbytes;
+#pragma unroll
+                for (int kb = 0; kb < K / 8; ++kb) {
+                    uint4 v;
+                    __half* hv = reinterpret_cast<__half*>(&v);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) hv[q] = row[kb * 8 + q];
+                    *reinterpret_cast<uint4*>(base + (((tid >> 3) * (K / 8) + kb) * 64 + (tid & 7) * 8) * 2) = v;
+                }
+            }
+        }
+        fence_proxy_async();     // generic-proxy writes of the operand rows -> tensor core
+        __syncthreads();
+
+        // ---- walk the tiles: MMA of tile i+1 overlaps the epilogue of tile i
+        float B1 = __int_as_float(0x7F800000), B2 = __int_as_float(0x7F800000);
+        int bc = 0;
+        int ci = -1, cj = -1;
+        bool needA = false, needB = false;
+        auto issue = [&](int i) {
+            // thread 0 only: wait for the tile, then the MMA into accumulator i & 1
+            const int slot = resident ? i : i % RS;
+            if (loaded_now || !resident) {
+                const uint32_t b = smem_u32(&s_bfull[slot]);
+                if (!mbar_wait_bounded(b, (bphase >> slot) & 1u, p.spin_budget)) {
+                    record_error(p.status, 4 /* QT_ETIMEOUT */, 11);
+                    s_abort = 1;
+                    mbar_wait_bounded(b, (bphase >> slot) & 1u, 1ll << 24);
+                }
+            }
+            tc_fence_after();
+            const uint32_t a_base = sA_u + (i < tA ? 0 : kAbytes);
+            const uint32_t b_base = sB_u + slot * kTileBytes;
+            const uint32_t dt = tmem + (uint32_t)((i & 1) * kTcTileN);
+#pragma unroll
+            for (int s = 0; s < KT; ++s) {
+                const uint64_t ad = smem_desc(a_base + s * 256, 128, K * 16);
+                const uint64_t bd = smem_desc(b_base + s * 256, 128, K * 16);
+                tc_mma(dt, ad, bd, idesc, s > 0 ? 1u : 0u);
+            }
+            tc_commit(smem_u32(&s_mma[i & 1]));
+        };
+        if (tid == 0) issue(0);
+        for (int i = 0; i < nT; ++i) {
+            const int slot = resident ? i : i % RS;
+            if (tid == 0 && i + 1 < nT) issue(i + 1);
+            // the barrier parities of tile i's slot advance once per load
+            if (loaded_now || !resident) bphase ^= (1u << slot);
+            const bool ok = mbar_wait_bounded(smem_u32(&s_mma[i & 1]), (mphase >> (i & 1)) & 1u, p.spin_budget);
+            if (!ok) {
+                if (tid == 0) {
+                    record_error(p.status, 4 /* QT_ETIMEOUT */, 12);
+                    s_abort = 1;
+                }
+                mbar_wait_bounded(smem_u32(&s_mma[i & 1]), (mphase >> (i & 1)) & 1u, 1ll << 24);
+            }
+            mphase ^= (1u << (i & 1));
+            tc_fence_after();
+            // epilogue: this thread's row, 256 scores in 16 chunks
+            const int lt = i < tA ? i : i - tA;
+#pragma unroll
+            for (int q = 0; q < kTcTileN / 32; ++q) {
+                float v[32];
+                tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((i & 1) * kTcTileN + q * 32), v);
+                tc_wait_ld();
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float mc = min16(v + 16 * h);
+                    const int c = lt * (kTcTileN / kChunk) + q * 2 + h;
+                    B2 = fminf(B2, fmaxf(mc, B1));
+                    const bool nw = mc < B1;
+                    B1 = fminf(B1, mc);
+                    bc = nw ? c : bc;
+                }
+            }
+            tc_fence_before();
+            __syncthreads();      // accumulator i & 1 and (streamed) slot of tile i are free
+            if (tid == 0 && !resident && i + RS < nT) {
+                const uint32_t b = smem_u32(&s_bfull[slot]);
+                fence_proxy_async();
+                mbar_arrive_expect_tx(b, kTileBytes);
+                bulk_g2s(sB_u + slot * kTileBytes, tile_src(i + RS), kTileBytes, b);
+            }
+            if (i == tA - 1 || i == nT - 1) {
+                // grid done: re-score the best chunk in FP32 and certify
+                const bool isA = i == tA - 1;
+                const GridInfo& G = isA ? s_GA : s_GB;
+                const float inv_sg = ldexpf(1.0f, -G.tc_exp);
+                const float* recs = p.rec32 + G.roff * Rec32<DM>::kFloats;
+                int idx;
+                float best, S1, r1;
+                cc_chunk<DM>(recs, bc, isA ? cs.xa : cs.yb, idx, best, S1, r1);
+                const float B2cc = B2 * inv_sg * inv_sg;
+                const bool cert = tc_certified(d, isA ? cs.Aa : cs.Ab, best, S1, B2cc, r1, inv_sg) &&
+                                  idx < (isA ? L.NA : L.NB) && !(isA ? bigA : bigB);
+                if (isA) {
+                    ci = idx;
+                    needA = !cert && valid;
+                } else {
+                    cj = idx;
+                    needB = !cert && valid;
+                }
+                B1 = __int_as_float(0x7F800000);
+                B2 = __int_as_float(0x7F800000);
+                bc = 0;
+            }
+            if (s_abort) {
+                // the MMA of tile i + 1 may be in flight: let it finish before leaving
+                if (i + 1 < nT) {
+                    mbar_wait_bounded(smem_u32(&s_mma[(i + 1) & 1]), (mphase >> ((i + 1) & 1)) & 1u, 1ll << 24);
+                    mphase ^= (1u << ((i + 1) & 1));
+                }
+                break;
+            }
+        }
+        if (resident) loaded_now = false;
+        if (s_abort) break;
+
+        // ---- uncertified searches: warp FP32 re-screen, then the exact FP64 search
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const bool need = g == 0 ? needA : needB;
+            unsigned mask = __ballot_sync(0xFFFFFFFFu, need);
+            const GridInfo& G = g == 0 ? s_GA : s_GB;
+            while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                int r = warp_screen_nn<DM>(g == 0 ? cs.xa : cs.yb, g == 0 ? cs.Aa : cs.Ab, src,
+                                           p.rec32 + G.roff * Rec32<DM>::kFloats, G.Npad, d);
+                if (r < 0) {
+                    double z[DM];
+                    if (lane == src) exact_sample<DM>(p, s_pf, s_pd, k, ms, g == 1, z);
+                    r = warp_exact_nn<DM>(z, src, p.g64 + G.goff * d, G.N, d);
+                }
+                if (lane == src) {
+                    if (g == 0) ci = r; else cj = r;
+                }
+                if (lane == 0) atomicAdd(&p.status->rechecks, 1ull);
+            }
+        }
+
+        // ---- counters p^k_ij
+        if (valid) {
+            if ((unsigned)ci >= (unsigned)L.NA || (unsigned)cj >= (unsigned)L.NB) {
+                record_error(p.status, 6 /* QT_EDEVICE */, 13);
+            } else {
+                count_add(p.counts, p.counts_u32, L.coff + (long long)ci * L.NB + cj, 1u);
+                if (p.cellsA) {
+                    p.cellsA[ms] = ci;
+                    p.cellsB[ms] = cj;
+                }
+                if (p.dump_count > 0 && (ms % (unsigned long long)p.dump_stride) == 0ull) {
+                    const unsigned long long t = ms / (unsigned long long)p.dump_stride;
+                    if (t < (unsigned long long)p.dump_count) {
+                        const long long row = (long long)k * p.dump_count + (long long)t;
+                        double zx[DM], zy[DM];
+                        exact_sample<DM>(p, s_pf, s_pd, k, ms, false, zx);
+                        exact_sample<DM>(p, s_pf, s_pd, k, ms, true, zy);
+                        for (int l = 0; l < d; ++l) {
+                            p.dumpX[row * d + l] = zx[l];
+                            p.dumpY[row * d + l] = zy[l];
+                        }
+                        p.dumpI[row] = ci;
+                        p.dumpJ[row] = cj;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- release the tensor memory (every MMA issued has completed: each was waited)
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+    }
+}
+
+template <int DM, int KT>
+static cudaError_t launch_tc(const ForwardParams& p, int dyn, int num_sms, int* bps, cudaStream_t st)
+{
+    auto kern = forward_tc_kernel<DM, KT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return e;
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 128, dyn);
+    if (e != cudaSuccess) return e;
+    if (b != 1) return cudaErrorInvalidConfiguration;   // one CTA per SM: it owns all 512 TMEM columns
+    *bps = b;
+    long long grid = (long long)num_sms;
+    if (grid > p.total_items) grid = p.total_items;
+    kern<<<(unsigned)grid, 128, dyn, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_forward(int dm, const ForwardParams& p, int dyn, int num_sms, int* bps, cudaStream_t st)
+{
+    if (dm == 2) return launch_tc<2, 1>(p, dyn, num_sms, bps, st);
+    if (dm == 4) return launch_tc<4, 1>(p, dyn, num_sms, bps, st);
+    if (dm == 6) return launch_tc<6, 2>(p, dyn, num_sms, bps, st);
+    if (dm == 8) return launch_tc<8, 2>(p, dyn, num_sms, bps, st);
+    if (dm == 10) return launch_tc<10, 2>(p, dyn, num_sms, bps, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace qt

@@ -42,7 +42,13 @@ struct GridInfo {
     float R;                       // max norm of the centred FP32 records (rounded up)
     int32_t N, Npad;
     long long goff, roff;
+    int32_t tc_exp;                // tensor-core form: operands scaled by 2^tc_exp
+    int32_t tc_tiles;              // tensor-core form: 256-point operand tiles of this grid
+    long long tc_toff;             // tensor-core form: first tile of this grid
 };
+
+constexpr int kTcTileN = 256;      // grid points per tensor-core operand tile (MMA N)
+constexpr int kTcTileM = 128;      // samples per tensor-core work item (MMA M)
 
 struct ForwardParams {
     // problem
@@ -83,6 +89,11 @@ struct ForwardParams {
     int32_t* dumpI;
     int32_t* dumpJ;
     DevStatus* status;
+    // tensor-core form
+    const void* tc_tiles;          // FP16 operand tiles [tiles][256][K] in the canonical K-major layout
+    int32_t tc_k;                  // 16 or 32
+    int32_t tc_slots;              // ring slots of operand tiles in shared memory
+    int32_t tc_resident;           // 1: both grids' tiles stay in shared memory for the layer
 };
 
 }  // namespace qt

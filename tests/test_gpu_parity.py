@@ -128,6 +128,51 @@ def test_streamed_timeout_is_reported(ctx, B):
     assert int(counts.sum()) == model.n * model.M
 
 
+TC_CASES = [("ou2", 500, 20011, 6), ("basket4", 0, 9001, 3), ("ar8", 700, 5003, 2), ("ar8", 4000, 3001, 2),
+            ("maxcall10", 500, 3001, 2), ("maxcall10", 8000, 2003, 2)]
+
+
+@pytest.mark.parametrize("name,N,M,n", TC_CASES)
+def test_counts_bit_exact_tensor_core(ctx, B, name, N, M, n):
+    """tcgen05 screen: resident operand tiles (N <= a few thousand) and the
+    streamed ring (d = 8, N = 4000; d = 10, N = 8000), against the oracle."""
+    model = _model(name, M=M, n=n, N=N) if N else _model(name, M=M, n=n)
+    g = W.layer_grids(model, samples=max(20000, 3 * int(model.N[-1])), iters=3) if model.grid_kind == "kmeans" \
+        else W.layer_grids(model)
+    counts, stats, _ = ctx.transitions(model, _dev(g), model.M, model.seed, B.options(form=B.FORM_TC_RECHECK))
+    ref = oracle.transitions(model, g, model.M, model.seed, oracle.PREC_F32)
+    got = B.split_counts(model.N, counts.cpu().numpy())
+    for k in range(model.n):
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=f"layer {k}")
+    assert stats.device_status == 0 and stats.form_used == B.FORM_TC_RECHECK
+
+
+def test_tensor_core_adversarial_near_ties(ctx, B):
+    rng = np.random.default_rng(12)
+    for d, N in ((2, 300), (4, 600), (8, 900), (10, 700)):
+        gA = rng.standard_normal((N, d))
+        gB = rng.standard_normal((N + 37, d)) * 1.1
+        X = np.concatenate([W.boundary_samples(gA, 2000, seed=5), W.boundary_samples(gA, 2000, seed=6, jitter=1e-6),
+                            rng.standard_normal((2000, d)), rng.standard_normal((50, d)) * 40.0])
+        Y = np.concatenate([W.boundary_samples(gB, 2000, seed=7), W.boundary_samples(gB, 2000, seed=8, jitter=1e-8),
+                            rng.standard_normal((2050, d))])
+        counts, stats, ii, jj = ctx.counts_from_samples(_dev(gA), _dev(gB), _dev(X), _dev(Y),
+                                                        B.options(form=B.FORM_TC_RECHECK), want_cells=True)
+        np.testing.assert_array_equal(ii.cpu().numpy(), oracle.nearest(gA, X))
+        np.testing.assert_array_equal(jj.cpu().numpy(), oracle.nearest(gB, Y))
+        assert stats.rechecks > 100
+
+
+def test_tensor_core_timeout_is_reported(ctx, B):
+    model = _model("ar8", M=600, n=2, N=4000)
+    g = _dev(W.layer_grids(model, samples=12000, iters=2))
+    with pytest.raises(B.QtError) as e:
+        ctx.transitions(model, g, model.M, model.seed, B.options(form=B.FORM_TC_RECHECK, spin_budget=-1))
+    assert e.value.status == B.QT_ETIMEOUT
+    counts, _, _ = ctx.transitions(model, g, model.M, model.seed, B.options(form=B.FORM_TC_RECHECK))
+    assert int(counts.sum()) == model.n * model.M
+
+
 def test_dump_samples_and_cells_bit_exact(ctx, B):
     """Every drawn (X_k, Y) and both cells, against the oracle's own sampler and search."""
     model = _model("ou2", M=5000, n=3, N=200)
