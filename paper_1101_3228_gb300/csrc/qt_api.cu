@@ -485,7 +485,8 @@ bool stream_is_capturing(cudaStream_t st)
 qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long M, unsigned long long seed,
                           const qt_options* o, int source, void* dparams_f, void* dparams_d, const void* hparams_f,
                           const void* hparams_d, size_t pcount, void* dlayers, void* dgrids, const void* hlayers,
-                          const void* hgrids, void* drec32, void* drec64, DevStatus* dstatus, cudaStream_t st)
+                          const void* hgrids, void* drec32, void* drec64, DevStatus* dstatus, cudaStream_t st,
+                          void* dtiles)
 {
     QT_CUDA(cudaMemcpyAsync(dparams_f, hparams_f, pcount * 4, cudaMemcpyHostToDevice, st));
     QT_CUDA(cudaMemcpyAsync(dparams_d, hparams_d, pcount * 8, cudaMemcpyHostToDevice, st));
@@ -506,10 +507,7 @@ qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long
             P.form != kPlainF64 ? (float*)drec32 : nullptr, P.form == kPlainF64 ? (double*)drec64 : nullptr);
         QT_CUDA(cudaGetLastError());
     }
-    void* dtiles = nullptr;
     if (P.form == kTcRecheck) {
-        qt_status ts = dev_get(ctx, "tctiles", (size_t)P.tc_total_tiles * kTcTileN * P.tc_k * 2, &dtiles);
-        if (ts) return ts;
         const long long rows = P.tc_total_tiles * kTcTileN;
         prep_tc_tiles_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(
             (const float*)drec32, (GridInfo*)dgrids, P.ngrids, P.d, P.rec_floats, P.tc_k, rows, (__half*)dtiles);
@@ -623,6 +621,10 @@ qt_status run_plan(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long M, uns
         if ((s = dev_get(ctx, (tag + "rec64").c_str(), (size_t)P.total_recs * P.rec64 * 8, &drec64))) return s;
     }
     if ((s = dev_get(ctx, (tag + "status").c_str(), sizeof(DevStatus), &dstatus))) return s;
+    void* dtiles = nullptr;
+    if (P.form == kTcRecheck &&
+        (s = dev_get(ctx, (tag + "tctiles").c_str(), (size_t)P.tc_total_tiles * kTcTileN * P.tc_k * 2, &dtiles)))
+        return s;
     void *hlayers, *hgrids, *hpf, *hpd;
     if ((s = host_get(ctx, (tag + "layers").c_str(), sizeof(LayerDesc) * P.layers.size(), &hlayers))) return s;
     if ((s = host_get(ctx, (tag + "grids").c_str(), sizeof(GridInfo) * P.grids.size(), &hgrids))) return s;
@@ -645,7 +647,7 @@ qt_status run_plan(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long M, uns
     ctx->status_buf = dstatus;
     if (!use_graph) {
         s = enqueue_forward(ctx, P, io, M, seed, o, source, dpf, dpd, hpf, hpd, pbytes, dlayers, dgrids, hlayers,
-                            hgrids, drec32, drec64, (DevStatus*)dstatus, st);
+                            hgrids, drec32, drec64, (DevStatus*)dstatus, st, dtiles);
         if (s) return s;
     } else {
         // graph key: everything the enqueued work depends on
@@ -672,7 +674,7 @@ qt_status run_plan(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long M, uns
             QT_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
             qt_status es = enqueue_forward(ctx, P, io, M, seed, o, source, dpf, dpd, hpf, hpd, pbytes, dlayers,
                                            dgrids, hlayers, hgrids, drec32, drec64, (DevStatus*)dstatus,
-                                           ctx->cap_stream);
+                                           ctx->cap_stream, dtiles);
             cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
             if (es != QT_OK || ee != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
