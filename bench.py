@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--M", type=int, default=0, help="override samples per layer")
     ap.add_argument("--spt", type=int, default=0, help="samples per thread (0 = library choice)")
+    ap.add_argument("--router-samples", type=int, default=10**7, help="labelled pairs for the router form")
     return ap.parse_args()
 
 
@@ -238,14 +239,24 @@ def main():
     grids = ctx.build_grids(model, grid_method(model), samples=max(20 * int(np.max(model.N)), 200000),
                             iters=20, seed=W.GRID_SEED_BASE + W.CONFIG_INDEX[model.name])
     form = {"auto": B.FORM_AUTO, "plain_f64": B.FORM_PLAIN_F64, "f32_recheck": B.FORM_F32_RECHECK,
-            "tc_recheck": B.FORM_TC_RECHECK}.get(args.form, B.FORM_AUTO)
+            "tc_recheck": B.FORM_TC_RECHECK, "router_cert": B.FORM_ROUTER_CERT}.get(args.form, B.FORM_AUTO)
     if form == B.FORM_AUTO:
         form = default_form(model, B)
     prec = model.prec
     entries = int(np.sum(model.N[:-1] * model.N[1:]))
     # int64 counts unless they would take more than a quarter of the device (then uint32)
     ctype = B.COUNTS_I64 if entries * 8 <= torch.cuda.get_device_properties(dev).total_memory // 4 else B.COUNTS_U32
-    opts = B.options(form=form, prec=prec, samples_per_thread=args.spt, counts_type=ctype)
+    router = None
+    router_info = None
+    if form == B.FORM_ROUTER_CERT:
+        # trained before the timed region, on pairs the method itself labels
+        router = ctx.router_train(model, grids, samples=args.router_samples, layers=8, epochs=4, seed=7 +
+                                  W.CONFIG_INDEX[model.name])
+        ri = router.info()
+        router_info = {"train_samples": args.router_samples, "train_accuracy": ri.train_accuracy,
+                       "train_loss": ri.train_loss, "build_ms": ri.build_ms, "neighbours": ri.neighbours}
+    opts = B.options(form=form, prec=prec, samples_per_thread=args.spt, counts_type=ctype,
+                     router=router.handle if router else None)
     counts = torch.empty(entries, dtype=torch.int64 if ctype == B.COUNTS_I64 else torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # larger than the 129 MB L2
     units = model.n * model.M
@@ -280,6 +291,7 @@ def main():
 
     with ClockSampler(local) as clk:
         ms_step, kern_ms, rech = timed(opts, args.steps, max(3, args.warmup))
+    cand = ctx.status()[1].candidates
     clocks = clk.summary()
     if dist:
         t = torch.tensor([ms_step], device=dev)
@@ -346,7 +358,9 @@ def main():
                            "counts": "int64" if ctype == B.COUNTS_I64 else "uint32",
                            "sample_prec": "f32" if prec == 1 else "f64",
                            "l2": "256 MiB buffer written between timed steps",
-                           "rechecks_per_step": rech},
+                           "rechecks_per_step": rech,
+                           "router": router_info,
+                           "candidates_per_search": (cand / (2 * units)) if router else None},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
                 "clocks": clocks, "plain": plain}
         print(json.dumps(line), flush=True)

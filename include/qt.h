@@ -219,6 +219,65 @@ QT_API qt_status qt_get_status(qt_ctx* ctx, void* stream, qt_stats* stats);
  * shape (descriptor tables, prepared grids, status words).                   */
 QT_API qt_status qt_transitions_workspace(const qt_model* model, const qt_options* opts, size_t* bytes);
 
+/* ------------------------------------------------------------------------
+ * Learned router + Elkan certificate (search form QT_FORM_ROUTER_CERT).
+ * No paper counterpart for the network itself; the certificate restates the
+ * triangle inequality on the Voronoi cells of Sec. 2: if |x - c_i0| = r then the
+ * nearest cell j of x satisfies |c_i0 - c_j| <= 2r, so scanning the points of
+ * Gamma_k sorted by distance to c_i0 until that distance exceeds r + r* (r* the
+ * best distance found so far) finds the exact cell from any start cell i0.
+ * The router (an MLP d -> 64 -> 64 -> 64, ReLU, on whitened coordinates
+ * L_k^{-1}(x - m_k)) predicts which of 64 buckets (a k-means partition of the
+ * grid points) holds the cell; the start cell is the nearest member of that
+ * bucket.  A wrong prediction costs time, never exactness.
+ * Requires N_k equal for all k >= 1 (one bucket partition serves every layer)
+ * and 64 <= N_k <= 65535.                                                     */
+typedef struct qt_router qt_router;
+
+typedef struct {
+    int64_t train_samples;   /* labelled (sample, exact cell) pairs; 0 = 10^6            */
+    int32_t train_layers;    /* layers the pairs are drawn from (evenly spaced); 0 = 8    */
+    int32_t epochs;          /* passes over the pairs; 0 = 4                               */
+    int32_t batch;           /* minibatch; 0 = 4096                                        */
+    int32_t neighbours;      /* sorted neighbours kept per grid point (Elkan list); 0 = 256 */
+    float lr;                /* Adam step; 0 = 2e-3                                        */
+    int32_t untrained;       /* 1: keep the seeded initial weights (for comparisons)       */
+    int32_t reserved[3];
+} qt_router_config;
+
+typedef struct {
+    int64_t params;          /* number of FP32 parameters                                  */
+    int32_t d, buckets, hidden, neighbours;
+    double train_loss;       /* mean cross-entropy of the last epoch                       */
+    double train_accuracy;   /* top-1 bucket accuracy on the training pairs (last epoch)   */
+    double build_ms;         /* wall time of qt_router_train                               */
+} qt_router_info;
+
+/* Train a router for `model` and `grids` (dev FP64, concatenated as in
+ * qt_transitions): draws cfg->train_samples pairs (X_k, exact cell of X_k in
+ * Gamma_k) with the library's own sampler and search, trains the MLP with the
+ * library's own forward, backward and Adam kernels, and builds the bucket and
+ * neighbour tables of every grid.  The router is bound to these grids: a
+ * qt_transitions call with other grid values returns QT_EINVAL.  *out is owned
+ * by the caller (qt_router_destroy).  Synchronises the stream.                */
+QT_API qt_status qt_router_train(qt_ctx* ctx, const qt_model* model, const double* grids, const qt_router_config* cfg,
+                                 uint64_t seed, qt_router** out, void* stream);
+QT_API qt_status qt_router_destroy(qt_router* router);
+QT_API qt_status qt_router_get_info(const qt_router* router, qt_router_info* info);
+
+/* Copy the MLP parameters (FP32, packed W1[64][d], b1[64], W2[64][64], b2[64],
+ * W3[64][64], b3[64]) to host memory `out` (count floats) or set them from
+ * host memory `in`; count must equal info.params.                             */
+QT_API qt_status qt_router_get_params(const qt_router* router, float* out, int64_t count);
+QT_API qt_status qt_router_set_params(qt_router* router, const float* in, int64_t count);
+
+/* Mean cross-entropy over a batch and its gradient with respect to every
+ * parameter, from the library's own kernels (used to check them): z dev FP32
+ * [B][d], labels dev int32 [B] in [0, 64), grad dev FP32 [params] (written),
+ * loss host.  Synchronises the stream.                                        */
+QT_API qt_status qt_router_loss_grad(qt_ctx* ctx, const qt_router* router, const float* z, const int32_t* labels,
+                                     int64_t B, float* grad, double* loss, void* stream);
+
 /* Allocation-free counting step, for callers that cannot allocate device
  * memory (a host application whose allocator has reserved the device memory,
  * a plug-in that may not own device memory, or a latency-bound loop that cannot

@@ -29,7 +29,9 @@ FORM_NAMES = {FORM_AUTO: "auto", FORM_PLAIN_F64: "plain_f64", FORM_F32_RECHECK: 
 # every symbol include/qt.h declares (checked by the CPU test of the ABI)
 EXPORTS = ["qt_create", "qt_destroy", "qt_last_error", "qt_status_string", "qt_default_options",
            "qt_build_grids", "qt_transitions", "qt_counts_from_samples", "qt_backward", "qt_price",
-           "qt_get_status", "qt_transitions_workspace", "qt_counts_from_samples_noalloc"]
+           "qt_get_status", "qt_transitions_workspace", "qt_counts_from_samples_noalloc",
+           "qt_router_train", "qt_router_destroy", "qt_router_get_info", "qt_router_get_params",
+           "qt_router_set_params", "qt_router_loss_grad"]
 
 P = ctypes.c_void_p
 i32, i64, u32, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
@@ -51,6 +53,16 @@ class QtDump(ctypes.Structure):
 class QtStats(ctypes.Structure):
     _fields_ = [("samples", i64), ("rechecks", i64), ("searches", i64), ("candidates", i64),
                 ("form_used", i32), ("device_status", i32), ("ms", ctypes.c_double)]
+
+
+class QtRouterConfig(ctypes.Structure):
+    _fields_ = [("train_samples", i64), ("train_layers", i32), ("epochs", i32), ("batch", i32),
+                ("neighbours", i32), ("lr", ctypes.c_float), ("untrained", i32), ("reserved", i32 * 3)]
+
+
+class QtRouterInfo(ctypes.Structure):
+    _fields_ = [("params", i64), ("d", i32), ("buckets", i32), ("hidden", i32), ("neighbours", i32),
+                ("train_loss", ctypes.c_double), ("train_accuracy", ctypes.c_double), ("build_ms", ctypes.c_double)]
 
 
 class QtError(RuntimeError):
@@ -75,6 +87,12 @@ _SIGS = {
     "qt_get_status": (i32, [P, P, P]),
     "qt_transitions_workspace": (i32, [P, P, P]),
     "qt_counts_from_samples_noalloc": (i32, [i32, P, i64, P, i64, P, P, i64, i32, P, P, P, P]),
+    "qt_router_train": (i32, [P, P, P, P, u64, P, P]),
+    "qt_router_destroy": (i32, [P]),
+    "qt_router_get_info": (i32, [P, P]),
+    "qt_router_get_params": (i32, [P, P, i64]),
+    "qt_router_set_params": (i32, [P, P, i64]),
+    "qt_router_loss_grad": (i32, [P, P, P, P, i64, P, P, P]),
 }
 
 
@@ -258,6 +276,16 @@ class Context:
                                       _stream_ptr(stream)))
         return out.value, stats
 
+    def router_train(self, model, grids, samples: int = 200000, layers: int = 4, epochs: int = 4,
+                     batch: int = 4096, neighbours: int = 256, lr: float = 2e-3, untrained: bool = False,
+                     seed: int = 7, stream=None) -> "Router":
+        hm = HostModel(model)
+        cfg = QtRouterConfig(samples, layers, epochs, batch, neighbours, lr, 1 if untrained else 0)
+        h = P()
+        self._check(self.lib.qt_router_train(self.h, ctypes.byref(hm.c), _ptr(grids), ctypes.byref(cfg), seed,
+                                             ctypes.byref(h), _stream_ptr(stream)))
+        return Router(self, h)
+
     def status(self, stream=None):
         stats = QtStats()
         st = self.lib.qt_get_status(self.h, _stream_ptr(stream), ctypes.byref(stats))
@@ -269,6 +297,53 @@ class Context:
         out = ctypes.c_size_t(0)
         self._check(self.lib.qt_transitions_workspace(ctypes.byref(hm.c), ctypes.byref(opts), ctypes.byref(out)))
         return out.value
+
+
+class Router:
+    """A trained router (qt_router*), usable as options(form=FORM_ROUTER_CERT, router=r.handle)."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.h = h
+
+    @property
+    def handle(self):
+        return self.h.value
+
+    def info(self) -> QtRouterInfo:
+        out = QtRouterInfo()
+        self.ctx._check(self.lib.qt_router_get_info(self.h, ctypes.byref(out)))
+        return out
+
+    def params(self) -> np.ndarray:
+        n = self.info().params
+        out = np.empty(n, dtype=np.float32)
+        self.ctx._check(self.lib.qt_router_get_params(self.h, out.ctypes.data, n))
+        return out
+
+    def set_params(self, values) -> None:
+        v = np.ascontiguousarray(values, dtype=np.float32)
+        self.ctx._check(self.lib.qt_router_set_params(self.h, v.ctypes.data, v.size))
+
+    def loss_grad(self, z, labels, stream=None):
+        import torch
+        grad = torch.empty(self.info().params, dtype=torch.float32, device=z.device)
+        loss = ctypes.c_double(0.0)
+        self.ctx._check(self.lib.qt_router_loss_grad(self.ctx.h, self.h, _ptr(z), _ptr(labels), z.shape[0],
+                                                     _ptr(grad), ctypes.byref(loss), _stream_ptr(stream)))
+        return loss.value, grad
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.qt_router_destroy(self.h)
+            self.h = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def split_counts(N, flat):

@@ -28,6 +28,10 @@ __global__ void kmeans_assign_kernel(int, long long, const float*, int, const fl
 __global__ void kmeans_update_kernel(int, int, const unsigned long long*, const unsigned long long*, float*);
 __global__ void map_grid_kernel(int, int, const double*, const double*, const double*, double*);
 __global__ void prep_tc_tiles_kernel(const float*, GridInfo*, int, int, int, int, long long, __half*);
+cudaError_t launch_router_forward(int dm, const ForwardParams& p, int num_sms, int* bps, cudaStream_t st);
+cudaError_t launch_grid_checksum(const double* grids, long long count, unsigned long long* out, cudaStream_t st);
+void router_fill_params(const qt_router* r, ForwardParams& fp);
+bool router_matches(const qt_router* r, int d, int n, const int64_t* N);
 }  // namespace qt
 
 using namespace qt;
@@ -323,11 +327,21 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
     P.dm = dm_for(d);
     int form = o->form;
     if (form == QT_FORM_AUTO) form = QT_FORM_F32_RECHECK;
-    if (form == QT_FORM_ROUTER_CERT)
-        return fail(ctx, QT_EUNSUPPORTED, "search form %d is not available in this build", form);
-    if (form != QT_FORM_PLAIN_F64 && form != QT_FORM_F32_RECHECK && form != QT_FORM_TC_RECHECK)
+    if (form != QT_FORM_PLAIN_F64 && form != QT_FORM_F32_RECHECK && form != QT_FORM_TC_RECHECK &&
+        form != QT_FORM_ROUTER_CERT)
         return fail(ctx, QT_EINVAL, "unknown search form %d", form);
-    P.form = form == QT_FORM_PLAIN_F64 ? kPlainF64 : (form == QT_FORM_TC_RECHECK ? kTcRecheck : kF32Recheck);
+    P.form = form == QT_FORM_PLAIN_F64 ? kPlainF64
+                                       : (form == QT_FORM_TC_RECHECK ? kTcRecheck
+                                                                     : (form == QT_FORM_ROUTER_CERT ? kRouterCert
+                                                                                                    : kF32Recheck));
+    if (P.form == kRouterCert) {
+        const qt_router* rt = static_cast<const qt_router*>(o->router);
+        if (!rt) return fail(ctx, QT_EINVAL, "QT_FORM_ROUTER_CERT needs opts->router");
+        if (from_arrays) return fail(ctx, QT_EUNSUPPORTED, "the router form draws its own samples");
+        if (o->sample_prec != QT_PREC_F32) return fail(ctx, QT_EUNSUPPORTED, "the router form uses FP32 samples");
+        if (!router_matches(rt, d, n, Ns)) return fail(ctx, QT_EINVAL, "model shape differs from the router's");
+        P.dm = d <= 2 ? 2 : (d <= 4 ? 4 : (d <= 6 ? 6 : (d <= 8 ? 8 : (d <= 10 ? 10 : (d <= 12 ? 12 : 16)))));
+    }
     if (P.form == kTcRecheck) {
         if (d > 10) return fail(ctx, QT_EUNSUPPORTED, "the tensor-core screen needs d <= 10 (3d + 2 <= 32 columns)");
         P.dm = d <= 2 ? 2 : (d <= 4 ? 4 : (d <= 6 ? 6 : (d <= 8 ? 8 : 10)));
@@ -356,6 +370,39 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
         roff += G.Npad;
     }
     P.total_recs = roff;
+    if (P.form == kRouterCert) {
+        P.S = 1;
+        P.block = 128;
+        P.tile = 128;
+        P.grid_bytes = 0;
+        P.hist_bytes = 0;
+        P.dyn_smem = 0;
+        P.layers.resize(n);
+        long long item = 0, coff = 0;
+        const long long items_per_layer = (M + P.tile - 1) / P.tile;
+        for (int k = 0; k < n; ++k) {
+            LayerDesc& L = P.layers[k];
+            memset(&L, 0, sizeof L);
+            L.NA = (int)Ns[k];
+            L.NB = (int)Ns[k + 1];
+            L.NApad = P.grids[k].Npad;
+            L.NBpad = P.grids[k + 1].Npad;
+            L.gridA = k;
+            L.gridB = k + 1;
+            L.goffA = P.grids[k].goff;
+            L.goffB = P.grids[k + 1].goff;
+            L.roffA = P.grids[k].roff;
+            L.roffB = P.grids[k + 1].roff;
+            L.coff = coff;
+            L.item_begin = item;
+            L.items = (int)items_per_layer;
+            item += items_per_layer;
+            coff += (long long)L.NA * L.NB;
+        }
+        P.total_items = item;
+        P.count_entries = coff;
+        return QT_OK;
+    }
     if (P.form == kTcRecheck) {
         // one CTA of 128 threads per SM owns all 512 TMEM columns; operand tiles in a ring
         P.tc_k = P.dm <= 4 ? 16 : 32;
@@ -557,6 +604,13 @@ qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long
         fp.dumpJ = io.dump->j;
     }
     fp.status = dstatus;
+    if (P.form == kRouterCert) {
+        router_fill_params(static_cast<const qt_router*>(o->router), fp);
+        long long pts = 0;
+        for (const GridInfo& G : P.grids) pts += G.N;
+        cudaError_t ce = launch_grid_checksum(io.g64, pts * P.d, &dstatus->spare[0], st);
+        if (ce != cudaSuccess) return fail(ctx, QT_ECUDA, "grid checksum: %s", cudaGetErrorString(ce));
+    }
     int blocks_per_sm = 0;
     // timing events around the kernel; inside a capture they must be external
     // event nodes to be recorded at every replay
@@ -590,6 +644,7 @@ qt_status read_status(qt_ctx* ctx, cudaStream_t st, qt_stats* stats, long long s
         cudaGetLastError();
     }
     if (hs.code == QT_ETIMEOUT) return fail(ctx, QT_ETIMEOUT, "a bounded device wait ran out (site %d)", hs.where);
+    if (hs.code == QT_EINVAL) return fail(ctx, QT_EINVAL, "the grids differ from those the router was built for");
     if (hs.code != 0) return fail(ctx, QT_EDEVICE, "kernel reported status %d at site %d", hs.code, hs.where);
     return QT_OK;
 }
@@ -776,7 +831,7 @@ qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
     qt_status s = make_plan(ctx, d, n, Ns, mus, M, o, source == kArrays, P);
     if (s) return s;
     const bool capturing = stream_is_capturing(st);
-    if (P.form != kTcRecheck && o->tile_samples_per_thread <= 0 && !(o->flags & QT_FLAG_NO_TUNE) && !capturing &&
+    if (P.form != kTcRecheck && P.form != kRouterCert && o->tile_samples_per_thread <= 0 && !(o->flags & QT_FLAG_NO_TUNE) && !capturing &&
         o->spin_budget >= 0) {
         const TuneKey key = tune_key(P, source == kArrays ? 0 : o->sample_prec, Ns, n);
         if (!ctx->tune.count(key)) {
@@ -788,8 +843,10 @@ qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
         if ((s = make_plan(ctx, d, n, Ns, mus, M, &to, source == kArrays, P2))) return s;
         P = P2;
     }
-    ctx->last_form = P.form == kPlainF64 ? QT_FORM_PLAIN_F64
-                                         : (P.form == kTcRecheck ? QT_FORM_TC_RECHECK : QT_FORM_F32_RECHECK);
+    ctx->last_form = P.form == kPlainF64    ? QT_FORM_PLAIN_F64
+                     : P.form == kTcRecheck ? QT_FORM_TC_RECHECK
+                     : P.form == kRouterCert ? QT_FORM_ROUTER_CERT
+                                             : QT_FORM_F32_RECHECK;
     const bool use_graph = !(o->flags & QT_FLAG_NO_GRAPH) && !capturing;
     if ((s = run_plan(ctx, P, io, M, seed, o, source, params_d_host, st, use_graph, ""))) return s;
     if (stats) return read_status(ctx, st, stats, (long long)n * M, 2ll * n * M);

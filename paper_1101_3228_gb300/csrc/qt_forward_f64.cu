@@ -28,6 +28,7 @@ bool forward_variant_exists(int form, int dm, int S, bool streamed)
     static const int f32s[][2] = {{4, 1}, {4, 2}, {4, 4}, {6, 1}, {6, 2}, {6, 4}, {8, 1}, {8, 2}, {8, 4},
                                   {10, 1}, {10, 2}, {10, 4}, {12, 1}, {12, 2}, {16, 1}, {16, 2}};
     if (form == kTcRecheck) return S == 1 && (dm == 2 || dm == 4 || dm == 6 || dm == 8 || dm == 10);
+    if (form == kRouterCert) return S == 1;
     if (streamed) return form == kF32Recheck && in_list(dm, S, f32s, (int)(sizeof f32s / sizeof f32s[0]));
     static const int f32[][2] = {{1, 2}, {1, 4}, {1, 8}, {2, 2}, {2, 4}, {2, 8}, {3, 2}, {3, 4}, {3, 8},
                                  {4, 2}, {4, 4}, {4, 8}, {6, 1}, {6, 2}, {6, 4}, {8, 1}, {8, 2}, {8, 4},
@@ -43,6 +44,7 @@ cudaError_t forward_launch(int form, int dm, int S, bool streamed, const Forward
                            int num_sms, int* blocks_per_sm, cudaStream_t st)
 {
     if (form == kTcRecheck) return launch_tc_forward(dm, p, dyn_smem, num_sms, blocks_per_sm, st);
+    if (form == kRouterCert) return launch_router_forward(dm, p, num_sms, blocks_per_sm, st);
     if (streamed) {
         if (form != kF32Recheck) return cudaErrorInvalidValue;
         return launch_f32_streamed(dm, S, p, block, dyn_smem, num_sms, blocks_per_sm, st);

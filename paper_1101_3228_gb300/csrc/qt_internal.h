@@ -94,6 +94,20 @@ struct ForwardParams {
     int32_t tc_k;                  // 16 or 32
     int32_t tc_slots;              // ring slots of operand tiles in shared memory
     int32_t tc_resident;           // 1: both grids' tiles stay in shared memory for the layer
+    // learned router + Elkan certificate
+    const float* rt_params;        // MLP parameters, packed W1, b1, W2, b2, W3, b3
+    const float* rt_linv;          // [n+1][d][d] FP32 inverse Cholesky factors (whitening)
+    const int32_t* rt_bstart;      // [65] bucket starts into rt_members
+    const int32_t* rt_members;     // [N] grid indices sorted by bucket
+    const int32_t* rt_nb_idx;      // [n+1][N][C] neighbours of each grid point, nearest first
+    const float* rt_nb_dist;       // [n+1][N][C] their distances, rounded down
+    int32_t rt_C;                  // neighbours per point
+    int32_t rt_N;                  // common grid size of layers >= 1
+    unsigned long long rt_checksum;// checksum of the grids the router was built for
 };
+
+constexpr int kRtHidden = 64;      // router MLP width
+constexpr int kRtBuckets = 64;     // router classes (buckets of grid points)
+__host__ __device__ constexpr int rt_param_count(int d) { return kRtHidden * d + kRtHidden + 2 * (kRtHidden * kRtHidden + kRtHidden); }
 
 }  // namespace qt

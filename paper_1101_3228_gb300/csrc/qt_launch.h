@@ -20,6 +20,7 @@ cudaError_t launch_f32_large(int dm, int S, const ForwardParams& p, int block, i
                              cudaStream_t st);
 cudaError_t launch_f64(int dm, int S, const ForwardParams& p, int block, int dyn, int num_sms, int* bps,
                        cudaStream_t st);
+cudaError_t launch_router_forward(int dm, const ForwardParams& p, int num_sms, int* bps, cudaStream_t st);
 cudaError_t launch_tc_forward(int dm, const ForwardParams& p, int dyn, int num_sms, int* bps, cudaStream_t st);
 cudaError_t launch_f32_streamed(int dm, int S, const ForwardParams& p, int block, int dyn, int num_sms, int* bps,
                                 cudaStream_t st);

@@ -401,3 +401,39 @@ def test_lloyd_1d_grid_is_stationary():
     assert np.max(np.abs(mean - x)) < 1e-12
     D = W.distortion_1d(x)
     assert abs(100 ** 2 * D - 2.6671) < 1e-3       # Zador asymptote sqrt(3) pi / 2 = 2.72
+
+
+# --------------------------------------------------------------------------- router network reference
+
+def test_router_mlp_gradient_matches_finite_differences():
+    from oracle import router_mlp as R
+    rng = np.random.default_rng(21)
+    d, B = 5, 37
+    P = rng.standard_normal(R.count(d)) * 0.3
+    Z = rng.standard_normal((B, d))
+    y = rng.integers(0, 64, B)
+    L, g = R.loss_and_grad(P, Z, y)
+    assert abs(L - R.loss(P, Z, y)) < 1e-12
+    idx = rng.choice(P.size, 60, replace=False)
+    h = 1e-6
+    for i in idx:
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        fd = (R.loss(Pp, Z, y) - R.loss(Pm, Z, y)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+def test_router_mlp_zero_network_is_uniform():
+    from oracle import router_mlp as R
+    d = 3
+    P = np.zeros(R.count(d))
+    Z = np.random.default_rng(1).standard_normal((10, d))
+    L, g = R.loss_and_grad(P, Z, np.arange(10))
+    assert abs(L - math.log(64)) < 1e-14
+    # zero hidden activations: only the output biases receive gradient, mean(p - onehot)
+    gb3 = g[-64:]
+    assert np.allclose(g[:-64], 0.0)
+    ref = np.full(64, 1 / 64)
+    ref[np.arange(10)] -= 0.1
+    np.testing.assert_allclose(gb3, ref, atol=1e-15)
