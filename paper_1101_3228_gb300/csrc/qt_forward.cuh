@@ -460,6 +460,54 @@ __device__ __forceinline__ bool screen_certified(int d, float A, float B1, float
     return (second - B1) > thr;
 }
 
+// Whole-warp FP32 re-screen of one lane's sample over a grid (records in global
+// memory); returns the certified cell or -1.
+template <int DM>
+__device__ __noinline__ int warp_screen_nn(const float (&xs)[DM], float A, int src, const float* __restrict__ recs,
+                                           int Npad, int d)
+{
+    constexpr int F = Rec32<DM>::kFloats;
+    float x[DM];
+#pragma unroll
+    for (int l = 0; l < DM; ++l) x[l] = __shfl_sync(0xFFFFFFFFu, xs[l], src);
+    const float Av = __shfl_sync(0xFFFFFFFFu, A, src);
+    const int lane = threadIdx.x & 31;
+    float b1 = __int_as_float(0x7F800000), b2 = __int_as_float(0x7F800000);
+    int i1 = 0x7FFFFFFF;
+    for (int j = lane; j < Npad; j += 32) {
+        const float* r = recs + j * F;
+        float sc = r[0];
+#pragma unroll
+        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], r[1 + l], sc);
+        if (sc < b1) {
+            b2 = b1;
+            b1 = sc;
+            i1 = j;
+        } else {
+            b2 = fminf(b2, sc);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const float ob1 = __shfl_xor_sync(0xFFFFFFFFu, b1, off);
+        const float ob2 = __shfl_xor_sync(0xFFFFFFFFu, b2, off);
+        const int oi = __shfl_xor_sync(0xFFFFFFFFu, i1, off);
+        if (ob1 < b1 || (ob1 == b1 && oi < i1)) {
+            b2 = fminf(ob2, b1);
+            b1 = ob1;
+            i1 = oi;
+        } else {
+            b2 = fminf(b2, ob1);
+        }
+    }
+    const float* r = recs + i1 * F;
+    float n2 = 0.0f;
+#pragma unroll
+    for (int l = 0; l < DM; ++l) n2 = __fmaf_rn(r[1 + l], r[1 + l], n2);
+    return screen_certified(d, Av, b1, b2, __fsqrt_rn(n2)) ? i1 : -1;
+}
+
+
 // ------------------------------------------------------------------ the kernel
 
 // Small dimension classes keep two CTAs (16 warps) resident per SM.

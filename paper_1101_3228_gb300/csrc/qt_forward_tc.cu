@@ -155,53 +155,6 @@ __device__ __forceinline__ bool tc_certified(int d, float A, float best, float S
     return lhs - rhs > 0x1p-20f * (fabsf(lhs) + fabsf(rhs)) + eta;
 }
 
-// Whole-warp FP32 re-screen of one lane's sample over a grid (records in global
-// memory); returns the certified cell or -1.
-template <int DM>
-__device__ __noinline__ int warp_screen_nn(const float (&xs)[DM], float A, int src, const float* __restrict__ recs,
-                                           int Npad, int d)
-{
-    constexpr int F = Rec32<DM>::kFloats;
-    float x[DM];
-#pragma unroll
-    for (int l = 0; l < DM; ++l) x[l] = __shfl_sync(0xFFFFFFFFu, xs[l], src);
-    const float Av = __shfl_sync(0xFFFFFFFFu, A, src);
-    const int lane = threadIdx.x & 31;
-    float b1 = __int_as_float(0x7F800000), b2 = __int_as_float(0x7F800000);
-    int i1 = 0x7FFFFFFF;
-    for (int j = lane; j < Npad; j += 32) {
-        const float* r = recs + j * F;
-        float sc = r[0];
-#pragma unroll
-        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], r[1 + l], sc);
-        if (sc < b1) {
-            b2 = b1;
-            b1 = sc;
-            i1 = j;
-        } else {
-            b2 = fminf(b2, sc);
-        }
-    }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        const float ob1 = __shfl_xor_sync(0xFFFFFFFFu, b1, off);
-        const float ob2 = __shfl_xor_sync(0xFFFFFFFFu, b2, off);
-        const int oi = __shfl_xor_sync(0xFFFFFFFFu, i1, off);
-        if (ob1 < b1 || (ob1 == b1 && oi < i1)) {
-            b2 = fminf(ob2, b1);
-            b1 = ob1;
-            i1 = oi;
-        } else {
-            b2 = fminf(b2, ob1);
-        }
-    }
-    const float* r = recs + i1 * F;
-    float n2 = 0.0f;
-#pragma unroll
-    for (int l = 0; l < DM; ++l) n2 = __fmaf_rn(r[1 + l], r[1 + l], n2);
-    return screen_certified(d, Av, b1, b2, __fsqrt_rn(n2)) ? i1 : -1;
-}
-
 }  // namespace
 
 // FP16 operand tiles of every grid: row j of grid g (tile j/256) holds
@@ -254,7 +207,7 @@ __global__ void prep_tc_tiles_kernel(const float* __restrict__ rec32, GridInfo* 
 }
 
 template <int DM, int KT>
-__global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams p)
+__global__ void __launch_bounds__(128, 2) forward_tc_kernel(const ForwardParams p)
 {
     constexpr int K = 16 * KT;
     constexpr int kTileBytes = kTcTileN * K * 2;
@@ -288,7 +241,7 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(512u)
+                     "r"((uint32_t)(2 * kTcTileN))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -367,9 +320,14 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
             const float sgA = ldexpf(1.0f, s_GA.tc_exp), sgB = ldexpf(1.0f, s_GB.tc_exp);
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
-                __half row[K];
+                unsigned char* base = sA + g * kAbytes;
+                // zero the row, then scatter [a_hi, a_hi, a_lo, 1, 1] into its K columns
 #pragma unroll
-                for (int q = 0; q < K; ++q) row[q] = __float2half_rn(0.0f);
+                for (int kb = 0; kb < K / 8; ++kb)
+                    *reinterpret_cast<uint4*>(base + (((tid >> 3) * (K / 8) + kb) * 64 + (tid & 7) * 8) * 2) =
+                        make_uint4(0u, 0u, 0u, 0u);
+                __half* hrow = reinterpret_cast<__half*>(base);
+                auto at = [&](int q) -> __half& { return hrow[((tid >> 3) * (K / 8) + (q >> 3)) * 64 + (tid & 7) * 8 + (q & 7)]; };
                 bool big = false;
 #pragma unroll
                 for (int l = 0; l < DM; ++l) {
@@ -378,26 +336,17 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
                 }
 #pragma unroll
                 for (int l = 0; l < DM; ++l) {
-                    const float v = big ? 0.0f : (g == 0 ? sgA * cs.xa[l] : sgB * cs.yb[l]);
-                    const __half h = __float2half_rn(v);
                     if (l < d) {
-                        row[l] = h;
-                        row[d + l] = h;
-                        row[2 * d + l] = __float2half_rn(v - __half2float(h));
+                        const float v = big ? 0.0f : (g == 0 ? sgA * cs.xa[l] : sgB * cs.yb[l]);
+                        const __half h = __float2half_rn(v);
+                        at(l) = h;
+                        at(d + l) = h;
+                        at(2 * d + l) = __float2half_rn(v - __half2float(h));
                     }
                 }
+                at(3 * d) = __float2half_rn(1.0f);
+                at(3 * d + 1) = __float2half_rn(1.0f);
                 if (g == 0) bigA = big; else bigB = big;
-                row[3 * d] = __float2half_rn(1.0f);
-                row[3 * d + 1] = __float2half_rn(1.0f);
-                unsigned char* base = sA + g * kAbytes;
-#pragma unroll
-                for (int kb = 0; kb < K / 8; ++kb) {
-                    uint4 v;
-                    __half* hv = reinterpret_cast<__half*>(&v);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) hv[q] = row[kb * 8 + q];
-                    *reinterpret_cast<uint4*>(base + (((tid >> 3) * (K / 8) + kb) * 64 + (tid & 7) * 8) * 2) = v;
-                }
             }
         }
         fence_proxy_async();     // generic-proxy writes of the operand rows -> tensor core
@@ -565,7 +514,9 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
     __syncthreads();
     tc_fence_after();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)(2 * kTcTileN))
+                     : "memory");
     }
 }
 
@@ -578,9 +529,9 @@ static cudaError_t launch_tc(const ForwardParams& p, int dyn, int num_sms, int* 
     int b = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 128, dyn);
     if (e != cudaSuccess) return e;
-    if (b != 1) return cudaErrorInvalidConfiguration;   // one CTA per SM: it owns all 512 TMEM columns
+    if (b < 1 || b > 2) return cudaErrorInvalidConfiguration;   // at most two CTAs per SM: 2 x 256 TMEM columns
     *bps = b;
-    long long grid = (long long)num_sms;
+    long long grid = (long long)num_sms * b;
     if (grid > p.total_items) grid = p.total_items;
     kern<<<(unsigned)grid, 128, dyn, st>>>(p);
     return cudaGetLastError();

@@ -355,14 +355,28 @@ __device__ __noinline__ RouteOut<DM> route_search(const ForwardParams& p, const 
     // router
     float h1[kRtHidden], h2[kRtHidden], lg[kRtBuckets];
     mlp_forward<DM>(sP, d, z, h1, h2, lg);
-    int bk = 0;
-    float mx = lg[0];
+    // the two highest logits
+    int bk = 0, bk2 = 1;
+    float mx = lg[0], mx2 = lg[1];
+    if (mx2 > mx) {
+        bk = 1;
+        bk2 = 0;
+        const float t = mx;
+        mx = mx2;
+        mx2 = t;
+    }
 #pragma unroll
-    for (int o = 1; o < kRtBuckets; ++o)
+    for (int o = 2; o < kRtBuckets; ++o) {
         if (lg[o] > mx) {
+            mx2 = mx;
+            bk2 = bk;
             mx = lg[o];
             bk = o;
+        } else if (lg[o] > mx2) {
+            mx2 = lg[o];
+            bk2 = o;
         }
+    }
     auto score = [&](int j) {
         const float* r = recs + (long long)j * F;
         float sc = __ldg(r);
@@ -370,19 +384,22 @@ __device__ __noinline__ RouteOut<DM> route_search(const ForwardParams& p, const 
         for (int l = 0; l < DM; ++l) sc = __fmaf_rn(xs[l], __ldg(r + 1 + l), sc);
         return sc;
     };
-    // start cell: nearest member of the predicted bucket
+    // start cell: nearest member of the two most likely buckets
     int i0 = -1;
     float s0 = __int_as_float(0x7F800000);
-    const int bs = p.rt_bstart[bk], be = p.rt_bstart[bk + 1];
-    for (int t = bs; t < be; ++t) {
-        const int j = p.rt_members[t];
-        const float sc = score(j);
-        if (sc < s0) {
-            s0 = sc;
-            i0 = j;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int b = pass == 0 ? bk : bk2;
+        const int bs = p.rt_bstart[b], be = p.rt_bstart[b + 1];
+        for (int t = bs; t < be; ++t) {
+            const int j = p.rt_members[t];
+            const float sc = score(j);
+            if (sc < s0) {
+                s0 = sc;
+                i0 = j;
+            }
         }
+        out.cands += be - bs;
     }
-    out.cands = be - bs;
     if (i0 < 0) return out;
     // Elkan walk over the neighbours of i0
     const float Eg = (float)(d + 2) * 0x1p-22f * (A + G.R) * (A + G.R);
@@ -506,10 +523,21 @@ __global__ void __launch_bounds__(128, 2) forward_router_kernel(const ForwardPar
 #pragma unroll
             for (int l = 0; l < DM; ++l) z[l] = (double)(g == 0 ? X[l] : Y[l]);
             const GridInfo& G = g == 0 ? s_GA : s_GB;
+            // centred FP32 copy for the warp re-screen
+            float xs[DM];
+            float A2 = 0.0f;
+#pragma unroll
+            for (int l = 0; l < DM; ++l) {
+                const float xh = l < d ? __fsub_rn(g == 0 ? X[l] : Y[l], G.mu[l]) : 0.0f;
+                xs[l] = -2.0f * xh;
+                A2 = __fmaf_rn(xh, xh, A2);
+            }
+            const float A = __fsqrt_rn(A2);
             while (mask) {
                 const int src = __ffs(mask) - 1;
                 mask &= mask - 1;
-                const int r = warp_exact_nn<DM>(z, src, p.g64 + G.goff * d, G.N, d);
+                int r = warp_screen_nn<DM>(xs, A, src, p.rec32 + G.roff * Rec32<DM>::kFloats, G.Npad, d);
+                if (r < 0) r = warp_exact_nn<DM>(z, src, p.g64 + G.goff * d, G.N, d);
                 if (lane == src) {
                     if (g == 0) ci = r; else cj = r;
                 }
@@ -711,10 +739,10 @@ extern "C" qt_status qt_router_train(qt_ctx* ctx, const qt_model* model, const d
     if (cfg_in) cfg = *cfg_in;
     const long long S = cfg.train_samples > 0 ? cfg.train_samples : 1000000;
     const int TL = std::min(n, cfg.train_layers > 0 ? cfg.train_layers : 8);
-    const int epochs = cfg.epochs > 0 ? cfg.epochs : 4;
+    const int epochs = cfg.epochs > 0 ? cfg.epochs : 8;
     const int Bt = cfg.batch > 0 ? cfg.batch : 4096;
-    const int C = std::min<int>(cfg.neighbours > 0 ? cfg.neighbours : 256, (int)Nc - 1);
-    const float lr = cfg.lr > 0 ? cfg.lr : 2e-3f;
+    const int C = std::min<int>(cfg.neighbours > 0 ? cfg.neighbours : 1024, (int)Nc - 1);
+    const float lr = cfg.lr > 0 ? cfg.lr : 3e-3f;
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
