@@ -276,8 +276,8 @@ class Context:
                                       _stream_ptr(stream)))
         return out.value, stats
 
-    def router_train(self, model, grids, samples: int = 200000, layers: int = 4, epochs: int = 4,
-                     batch: int = 4096, neighbours: int = 256, lr: float = 2e-3, untrained: bool = False,
+    def router_train(self, model, grids, samples: int = 200000, layers: int = 4, epochs: int = 0,
+                     batch: int = 4096, neighbours: int = 0, lr: float = 0.0, untrained: bool = False,
                      seed: int = 7, stream=None) -> "Router":
         hm = HostModel(model)
         cfg = QtRouterConfig(samples, layers, epochs, batch, neighbours, lr, 1 if untrained else 0)

@@ -404,12 +404,12 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
         return QT_OK;
     }
     if (P.form == kTcRecheck) {
-        // two CTAs of 128 threads per SM, 256 TMEM columns each (two 128-column
-        // accumulators); operand tiles in a ring of about 80 KB, which also keeps
-        // the shared memory above a third of the SM so that no third CTA fits
+        // one CTA of 128 threads per SM owns the 512 TMEM columns (two 256-column
+        // accumulators); operand tiles in a ring of 128 KB, which also keeps the
+        // shared memory above half of the SM so that no second CTA fits
         P.tc_k = P.dm <= 4 ? 16 : 32;
         const size_t tile_bytes = (size_t)kTcTileN * P.tc_k * 2;
-        P.tc_slots = (int)std::min<size_t>(16, (80 * 1024) / tile_bytes);
+        P.tc_slots = (int)std::min<size_t>(16, (128 * 1024) / tile_bytes);
         int tmax = 0;
         for (int k = 0; k < n; ++k) tmax = std::max(tmax, P.grids[k].tc_tiles + P.grids[k + 1].tc_tiles);
         P.tc_resident = tmax <= P.tc_slots;

@@ -508,6 +508,96 @@ __device__ __noinline__ int warp_screen_nn(const float (&xs)[DM], float A, int s
 }
 
 
+// Exact cell of one lane's sample with almost no FP64 work.  The whole warp
+// screens the grid in FP32 (records in global memory) for the best score B1 at
+// index i1.  The exact FP64 argmin i* (and every point tied with it) has
+//   s_i* <= s_i1 + eta <= B1 + E(r1) + eta,  hence |g_i*| <= rho and
+//   s~_i* <= B1 + E(r1) + E(rho) + eta
+// (the bounds of screen_certified), so evaluating D64 only on the window
+// {j : s~_j <= B1 + E(r1) + E(rho) + eta} (with slack) and taking the lowest
+// index of the smallest D64 gives the contract's cell.  z: the lane's exact
+// FP64 sample, xs: -2 (sample - mu) in FP32, A: |sample - mu|.
+template <int DM>
+__device__ __noinline__ int warp_window_nn(const float (&xs)[DM], float A, const double (&z)[DM], int src,
+                                           const float* __restrict__ recs, int Npad, const double* __restrict__ g64,
+                                           int N, int d)
+{
+    constexpr int F = Rec32<DM>::kFloats;
+    float x[DM];
+    double zz[DM];
+#pragma unroll
+    for (int l = 0; l < DM; ++l) {
+        x[l] = __shfl_sync(0xFFFFFFFFu, xs[l], src);
+        zz[l] = __shfl_sync(0xFFFFFFFFu, z[l], src);
+    }
+    const float Av = __shfl_sync(0xFFFFFFFFu, A, src);
+    const int lane = threadIdx.x & 31;
+    float b1 = __int_as_float(0x7F800000);
+    int i1 = 0x7FFFFFFF;
+    for (int j = lane; j < N; j += 32) {
+        const float* r = recs + (long long)j * F;
+        float sc = r[0];
+#pragma unroll
+        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], r[1 + l], sc);
+        if (sc < b1) {
+            b1 = sc;
+            i1 = j;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const float ob = __shfl_xor_sync(0xFFFFFFFFu, b1, off);
+        const int oi = __shfl_xor_sync(0xFFFFFFFFu, i1, off);
+        if (ob < b1 || (ob == b1 && oi < i1)) {
+            b1 = ob;
+            i1 = oi;
+        }
+    }
+    // window bound (same bounds as the certificate, with slack)
+    const float* r = recs + (long long)i1 * F;
+    float n2 = 0.0f;
+#pragma unroll
+    for (int l = 0; l < DM; ++l) n2 = __fmaf_rn(r[1 + l], r[1 + l], n2);
+    const float Ap = Av * (1.0f + 0x1p-18f);
+    const float cd = (float)(d + 2) * 0x1p-24f * (1.0f + 0x1p-10f);
+    const float r1 = __fsqrt_rn(n2) * (1.0f + 0x1p-18f);
+    const float E1 = cd * (r1 * r1 + 2.0f * Ap * r1);
+    const float U = b1 + E1;
+    const float A2 = Ap * Ap;
+    const float eta = 0x1p-44f * (A2 + fabsf(b1) + E1);
+    const float rad = fmaxf(A2 + U + 0x1p-18f * (A2 + fabsf(U)) + eta, 0.0f);
+    const float rho = Ap + __fsqrt_rn(rad);
+    const float Erho = cd * (rho * rho + 2.0f * Ap * rho);
+    const float lim = b1 + (E1 + Erho + eta) * 1.25f + 0x1p-20f * fabsf(b1) + 0x1p-100f;
+    // exact distances on the window only
+    double best = __longlong_as_double(0x7FF0000000000000LL);
+    int bi = 0x7FFFFFFF;
+    for (int j = lane; j < N; j += 32) {
+        const float* rr = recs + (long long)j * F;
+        float sc = rr[0];
+#pragma unroll
+        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], rr[1 + l], sc);
+        if (sc <= lim) {
+            const double dj = dist64<DM>(zz, g64 + (long long)j * d, d);
+            if (dj < best) {
+                best = dj;
+                bi = j;
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const double ob = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+        const int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, off);
+        if (ob < best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+        }
+    }
+    (void)Npad;
+    return bi;
+}
+
 // ------------------------------------------------------------------ the kernel
 
 // Small dimension classes keep two CTAs (16 warps) resident per SM.
@@ -806,12 +896,18 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) forward_kernel(const F
                     if (mask == 0) continue;
                     double z[DM];
                     if (need) exact_sample<DM>(p, s_pf, s_pd, k, ms[s], g == 1, z);
-                    const double* g64 = p.g64 + (g == 0 ? s_GA.goff : s_GB.goff) * d;
+                    const GridInfo& G = g == 0 ? s_GA : s_GB;
+                    const double* g64 = p.g64 + G.goff * d;
                     const int N = g == 0 ? L.NA : L.NB;
+                    float xsv[DM];
+#pragma unroll
+                    for (int l = 0; l < DM; ++l) xsv[l] = g == 0 ? xa[s][l] : yb[s][l];
+                    const float Av = g == 0 ? Aa[s] : Ab[s];
                     while (mask) {
                         const int src = __ffs(mask) - 1;
                         mask &= mask - 1;
-                        const int r = warp_exact_nn<DM>(z, src, g64, N, d);
+                        const int r = warp_window_nn<DM>(xsv, Av, z, src, p.rec32 + G.roff * Rec32<DM>::kFloats,
+                                                         G.Npad, g64, N, d);
                         if (lane == src) {
                             if (g == 0) ci[s] = r; else cj[s] = r;
                         }

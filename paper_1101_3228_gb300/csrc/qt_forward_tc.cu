@@ -207,7 +207,7 @@ __global__ void prep_tc_tiles_kernel(const float* __restrict__ rec32, GridInfo* 
 }
 
 template <int DM, int KT>
-__global__ void __launch_bounds__(128, 2) forward_tc_kernel(const ForwardParams p)
+__global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams p)
 {
     constexpr int K = 16 * KT;
     constexpr int kTileBytes = kTcTileN * K * 2;
@@ -465,13 +465,11 @@ __global__ void __launch_bounds__(128, 2) forward_tc_kernel(const ForwardParams 
             while (mask) {
                 const int src = __ffs(mask) - 1;
                 mask &= mask - 1;
-                int r = warp_screen_nn<DM>(g == 0 ? cs.xa : cs.yb, g == 0 ? cs.Aa : cs.Ab, src,
-                                           p.rec32 + G.roff * Rec32<DM>::kFloats, G.Npad, d);
-                if (r < 0) {
-                    double z[DM];
-                    if (lane == src) exact_sample<DM>(p, s_pf, s_pd, k, ms, g == 1, z);
-                    r = warp_exact_nn<DM>(z, src, p.g64 + G.goff * d, G.N, d);
-                }
+                double z[DM];
+                if (lane == src) exact_sample<DM>(p, s_pf, s_pd, k, ms, g == 1, z);
+                const int r = warp_window_nn<DM>(g == 0 ? cs.xa : cs.yb, g == 0 ? cs.Aa : cs.Ab, z, src,
+                                                 p.rec32 + G.roff * Rec32<DM>::kFloats, G.Npad,
+                                                 p.g64 + G.goff * d, G.N, d);
                 if (lane == src) {
                     if (g == 0) ci = r; else cj = r;
                 }
@@ -529,7 +527,7 @@ static cudaError_t launch_tc(const ForwardParams& p, int dyn, int num_sms, int* 
     int b = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 128, dyn);
     if (e != cudaSuccess) return e;
-    if (b < 1 || b > 2) return cudaErrorInvalidConfiguration;   // at most two CTAs per SM: 2 x 256 TMEM columns
+    if (b != 1) return cudaErrorInvalidConfiguration;   // one CTA per SM: it owns all 512 TMEM columns
     *bps = b;
     long long grid = (long long)num_sms * b;
     if (grid > p.total_items) grid = p.total_items;

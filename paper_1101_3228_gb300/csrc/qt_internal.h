@@ -47,7 +47,7 @@ struct GridInfo {
     long long tc_toff;             // tensor-core form: first tile of this grid
 };
 
-constexpr int kTcTileN = 128;      // grid points per tensor-core operand tile (MMA N)
+constexpr int kTcTileN = 256;      // grid points per tensor-core operand tile (MMA N)
 constexpr int kTcTileM = 128;      // samples per tensor-core work item (MMA M)
 
 struct ForwardParams {

@@ -536,8 +536,8 @@ __global__ void __launch_bounds__(128, 2) forward_router_kernel(const ForwardPar
             while (mask) {
                 const int src = __ffs(mask) - 1;
                 mask &= mask - 1;
-                int r = warp_screen_nn<DM>(xs, A, src, p.rec32 + G.roff * Rec32<DM>::kFloats, G.Npad, d);
-                if (r < 0) r = warp_exact_nn<DM>(z, src, p.g64 + G.goff * d, G.N, d);
+                const int r = warp_window_nn<DM>(xs, A, z, src, p.rec32 + G.roff * Rec32<DM>::kFloats, G.Npad,
+                                                 p.g64 + G.goff * d, G.N, d);
                 if (lane == src) {
                     if (g == 0) ci = r; else cj = r;
                 }
