@@ -135,8 +135,9 @@ __device__ __forceinline__ void cc_chunk(const float* __restrict__ recs, int chu
     r1 = __fsqrt_rn(n2);
 }
 
-// Mixed certificate: FP32 scores inside the best chunk, tensor-core scores
-// (B2tc: smallest chunk minimum outside it, FP32-score units) outside.
+// Mixed certificate: FP32 scores inside the two best chunks (best, S1: the
+// smallest other FP32 score there), tensor-core scores outside them (B2tc: the
+// smallest chunk minimum of the other chunks, FP32-score units).
 __device__ __forceinline__ bool tc_certified(int d, float A, float best, float S1, float B2tc, float r1,
                                              float inv_sigma)
 {
@@ -353,8 +354,9 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
         __syncthreads();
 
         // ---- walk the tiles: MMA of tile i+1 overlaps the epilogue of tile i
-        float B1 = __int_as_float(0x7F800000), B2 = __int_as_float(0x7F800000);
-        int bc = 0;
+        // per sample: best chunk (B1, bc), second chunk (Bs, bcs), smallest other chunk minimum B3
+        float B1 = __int_as_float(0x7F800000), Bs = __int_as_float(0x7F800000), B3 = __int_as_float(0x7F800000);
+        int bc = 0, bcs = 1;
         int ci = -1, cj = -1;
         bool needA = false, needB = false;
         auto issue = [&](int i) {
@@ -407,10 +409,12 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
                 for (int h = 0; h < 2; ++h) {
                     const float mc = min16(v + 16 * h);
                     const int c = lt * (kTcTileN / kChunk) + q * 2 + h;
-                    B2 = fminf(B2, fmaxf(mc, B1));
-                    const bool nw = mc < B1;
+                    const bool t1 = mc < B1, t2 = mc < Bs;
+                    B3 = fminf(B3, fmaxf(mc, Bs));
+                    Bs = fminf(Bs, fmaxf(mc, B1));
+                    bcs = t1 ? bc : (t2 ? c : bcs);
                     B1 = fminf(B1, mc);
-                    bc = nw ? c : bc;
+                    bc = t1 ? c : bc;
                 }
             }
             tc_fence_before();
@@ -422,16 +426,34 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
                 bulk_g2s(sB_u + slot * kTileBytes, tile_src(i + RS), kTileBytes, b);
             }
             if (i == tA - 1 || i == nT - 1) {
-                // grid done: re-score the best chunk in FP32 and certify
+                // grid done: re-score the two best chunks in FP32 and certify
                 const bool isA = i == tA - 1;
                 const GridInfo& G = isA ? s_GA : s_GB;
                 const float inv_sg = ldexpf(1.0f, -G.tc_exp);
                 const float* recs = p.rec32 + G.roff * Rec32<DM>::kFloats;
-                int idx;
-                float best, S1, r1;
+                const int nch = G.Npad / kChunk;      // chunks with FP32 records
+                int idx, idx2;
+                float best, S1, r1, best2, S12, r12;
                 cc_chunk<DM>(recs, bc, isA ? cs.xa : cs.yb, idx, best, S1, r1);
-                const float B2cc = B2 * inv_sg * inv_sg;
-                const bool cert = tc_certified(d, isA ? cs.Aa : cs.Ab, best, S1, B2cc, r1, inv_sg) &&
+                if (bcs < nch && bcs != bc) {
+                    cc_chunk<DM>(recs, bcs, isA ? cs.xa : cs.yb, idx2, best2, S12, r12);
+                } else {
+                    idx2 = idx;
+                    best2 = S12 = __int_as_float(0x7F800000);
+                    r12 = r1;
+                }
+                // merge the two chunks: lowest index among equal bests
+                float in2;
+                if (best2 < best || (best2 == best && idx2 < idx)) {
+                    in2 = fminf(S12, best);
+                    best = best2;
+                    idx = idx2;
+                    r1 = r12;
+                } else {
+                    in2 = fminf(S1, best2);
+                }
+                const float B3cc = B3 * inv_sg * inv_sg;
+                const bool cert = tc_certified(d, isA ? cs.Aa : cs.Ab, best, in2, B3cc, r1, inv_sg) &&
                                   idx < (isA ? L.NA : L.NB) && !(isA ? bigA : bigB);
                 if (isA) {
                     ci = idx;
@@ -440,9 +462,9 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
                     cj = idx;
                     needB = !cert && valid;
                 }
-                B1 = __int_as_float(0x7F800000);
-                B2 = __int_as_float(0x7F800000);
+                B1 = Bs = B3 = __int_as_float(0x7F800000);
                 bc = 0;
+                bcs = 1;
             }
             if (s_abort) {
                 // the MMA of tile i + 1 may be in flight: let it finish before leaving

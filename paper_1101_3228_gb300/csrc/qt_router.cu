@@ -323,6 +323,95 @@ struct RouteOut {
     int cands;      // candidate distances evaluated
 };
 
+// Forward pass of the router on transposed weights (shared memory):
+// W1T[l][o], W2T[i][o], W3T[i][o], so that one hidden input feeds 64 outputs
+// through 16 float4 loads.  Returns the two largest logits' buckets.
+template <int DM>
+__device__ __forceinline__ void mlp_route(const float* __restrict__ T, int d, const float (&z)[DM], int& bk, int& bk2)
+{
+    const float* W1T = T;
+    const float* b1 = W1T + kRtHidden * d;
+    const float* W2T = b1 + kRtHidden;
+    const float* b2 = W2T + kRtHidden * kRtHidden;
+    const float* W3T = b2 + kRtHidden;
+    const float* b3 = W3T + kRtHidden * kRtHidden;
+    float h[kRtHidden], g[kRtHidden];
+#pragma unroll
+    for (int o = 0; o < kRtHidden; ++o) h[o] = b1[o];
+#pragma unroll
+    for (int l = 0; l < DM; ++l) {
+        if (l < d) {
+            const float4* w = reinterpret_cast<const float4*>(W1T + l * kRtHidden);
+#pragma unroll
+            for (int q = 0; q < kRtHidden / 4; ++q) {
+                const float4 v = w[q];
+                h[4 * q + 0] = fmaf(v.x, z[l], h[4 * q + 0]);
+                h[4 * q + 1] = fmaf(v.y, z[l], h[4 * q + 1]);
+                h[4 * q + 2] = fmaf(v.z, z[l], h[4 * q + 2]);
+                h[4 * q + 3] = fmaf(v.w, z[l], h[4 * q + 3]);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < kRtHidden; ++o) {
+        h[o] = fmaxf(h[o], 0.0f);
+        g[o] = b2[o];
+    }
+#pragma unroll
+    for (int i = 0; i < kRtHidden; ++i) {
+        const float hi = h[i];
+        const float4* w = reinterpret_cast<const float4*>(W2T + i * kRtHidden);
+#pragma unroll
+        for (int q = 0; q < kRtHidden / 4; ++q) {
+            const float4 v = w[q];
+            g[4 * q + 0] = fmaf(v.x, hi, g[4 * q + 0]);
+            g[4 * q + 1] = fmaf(v.y, hi, g[4 * q + 1]);
+            g[4 * q + 2] = fmaf(v.z, hi, g[4 * q + 2]);
+            g[4 * q + 3] = fmaf(v.w, hi, g[4 * q + 3]);
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < kRtHidden; ++o) {
+        g[o] = fmaxf(g[o], 0.0f);
+        h[o] = b3[o];                      // h now holds the logits
+    }
+#pragma unroll
+    for (int i = 0; i < kRtHidden; ++i) {
+        const float gi = g[i];
+        const float4* w = reinterpret_cast<const float4*>(W3T + i * kRtHidden);
+#pragma unroll
+        for (int q = 0; q < kRtBuckets / 4; ++q) {
+            const float4 v = w[q];
+            h[4 * q + 0] = fmaf(v.x, gi, h[4 * q + 0]);
+            h[4 * q + 1] = fmaf(v.y, gi, h[4 * q + 1]);
+            h[4 * q + 2] = fmaf(v.z, gi, h[4 * q + 2]);
+            h[4 * q + 3] = fmaf(v.w, gi, h[4 * q + 3]);
+        }
+    }
+    bk = 0;
+    bk2 = 1;
+    float mx = h[0], mx2 = h[1];
+    if (mx2 > mx) {
+        bk = 1;
+        bk2 = 0;
+        const float t = mx;
+        mx = mx2;
+        mx2 = t;
+    }
+#pragma unroll
+    for (int o = 2; o < kRtBuckets; ++o) {
+        if (h[o] > mx) {
+            mx2 = mx;
+            bk2 = bk;
+            mx = h[o];
+            bk = o;
+        } else if (h[o] > mx2) {
+            mx2 = h[o];
+            bk2 = o;
+        }
+    }
+}
+
 // Routed, certified search of one point for grid G (records in global memory).
 template <int DM>
 __device__ __noinline__ RouteOut<DM> route_search(const ForwardParams& p, const float* __restrict__ sP,
@@ -353,30 +442,8 @@ __device__ __noinline__ RouteOut<DM> route_search(const ForwardParams& p, const 
     }
     const float A = __fsqrt_rn(A2);
     // router
-    float h1[kRtHidden], h2[kRtHidden], lg[kRtBuckets];
-    mlp_forward<DM>(sP, d, z, h1, h2, lg);
-    // the two highest logits
-    int bk = 0, bk2 = 1;
-    float mx = lg[0], mx2 = lg[1];
-    if (mx2 > mx) {
-        bk = 1;
-        bk2 = 0;
-        const float t = mx;
-        mx = mx2;
-        mx2 = t;
-    }
-#pragma unroll
-    for (int o = 2; o < kRtBuckets; ++o) {
-        if (lg[o] > mx) {
-            mx2 = mx;
-            bk2 = bk;
-            mx = lg[o];
-            bk = o;
-        } else if (lg[o] > mx2) {
-            mx2 = lg[o];
-            bk2 = o;
-        }
-    }
+    int bk, bk2;
+    mlp_route<DM>(sP, d, z, bk, bk2);
     auto score = [&](int j) {
         const float* r = recs + (long long)j * F;
         float sc = __ldg(r);
@@ -408,23 +475,42 @@ __device__ __noinline__ RouteOut<DM> route_search(const ForwardParams& p, const 
     float B1 = s0, S = __int_as_float(0x7F800000), rs = r0;
     int i1 = i0;
     const long long base = ((long long)gidx * p.rt_N + i0) * p.rt_C;
-    int c = 0;
-    for (; c < p.rt_C; ++c) {
-        const float dl = __ldg(p.rt_nb_dist + base + c);
-        if (dl > (r0 + rs) * (1.0f + 0x1p-20f)) break;
-        const int j = __ldg(p.rt_nb_idx + base + c);
-        const float sc = score(j);
-        if (sc < B1) {
-            S = B1;
-            B1 = sc;
-            i1 = j;
-            rs = rub(B1);
-        } else {
-            S = fminf(S, sc);
+    // walk the neighbours in blocks of 8 independent loads, then test in order
+    constexpr int kW = 8;
+    int scanned = 0;                 // neighbours taken as candidates
+    bool stop = false;               // the distance bound was reached inside the list
+    for (int c = 0; c < p.rt_C && !stop; c += kW) {
+        float dl[kW], sc[kW];
+        int jj[kW];
+#pragma unroll
+        for (int q = 0; q < kW; ++q) {
+            const int cq = min(c + q, p.rt_C - 1);
+            dl[q] = __ldg(p.rt_nb_dist + base + cq);
+            jj[q] = __ldg(p.rt_nb_idx + base + cq);
+        }
+#pragma unroll
+        for (int q = 0; q < kW; ++q) sc[q] = score(jj[q]);
+#pragma unroll
+        for (int q = 0; q < kW; ++q) {
+            if (stop || c + q >= p.rt_C) continue;
+            if (dl[q] > (r0 + rs) * (1.0f + 0x1p-20f)) {
+                stop = true;
+                continue;
+            }
+            ++scanned;
+            if (sc[q] < B1) {
+                S = B1;
+                B1 = sc[q];
+                i1 = jj[q];
+                rs = rub(B1);
+            } else {
+                S = fminf(S, sc[q]);
+            }
         }
     }
+    const int c = scanned;
     out.cands += c;
-    if (c == p.rt_C) return out;   // list exhausted before the bound: exact fallback
+    if (!stop) return out;          // list exhausted before the bound: exact fallback
     const float* r = recs + (long long)i1 * F;
     float n2 = 0.0f;
 #pragma unroll
@@ -445,8 +531,32 @@ __global__ void __launch_bounds__(128, 2) forward_router_kernel(const ForwardPar
     __shared__ __align__(16) double s_pd[param_count(DM)];
     const int tid = threadIdx.x, lane = tid & 31;
     const int d = p.d;
-    const int np = rt_param_count(d);
-    for (int e = tid; e < np; e += blockDim.x) sP[e] = p.rt_params[e];
+    // transposed copy of the parameters: W1T[l][o], b1, W2T[i][o], b2, W3T[i][o], b3
+    {
+        const float* W1 = p.rt_params;
+        const float* b1 = W1 + kRtHidden * d;
+        const float* W2 = b1 + kRtHidden;
+        const float* b2 = W2 + kRtHidden * kRtHidden;
+        const float* W3 = b2 + kRtHidden;
+        const float* b3 = W3 + kRtHidden * kRtHidden;
+        float* T1 = sP;
+        float* tb1 = T1 + kRtHidden * d;
+        float* T2 = tb1 + kRtHidden;
+        float* tb2 = T2 + kRtHidden * kRtHidden;
+        float* T3 = tb2 + kRtHidden;
+        float* tb3 = T3 + kRtHidden * kRtHidden;
+        for (int e = tid; e < kRtHidden * d; e += blockDim.x) T1[(e % d) * kRtHidden + e / d] = W1[e];
+        for (int e = tid; e < kRtHidden * kRtHidden; e += blockDim.x) {
+            T2[(e % kRtHidden) * kRtHidden + e / kRtHidden] = W2[e];
+            T3[(e % kRtHidden) * kRtHidden + e / kRtHidden] = W3[e];
+        }
+        for (int e = tid; e < kRtHidden; e += blockDim.x) {
+            tb1[e] = b1[e];
+            tb2[e] = b2[e];
+            tb3[e] = b3[e];
+        }
+    }
+    __syncthreads();
     // grids must be those the router was built for
     if (p.status->spare[0] != p.rt_checksum) {
         if (tid == 0) record_error(p.status, 1 /* QT_EINVAL */, 21);
