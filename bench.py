@@ -291,7 +291,9 @@ def main():
 
     with ClockSampler(local) as clk:
         ms_step, kern_ms, rech = timed(opts, args.steps, max(3, args.warmup))
-    cand = ctx.status()[1].candidates
+    _st = ctx.status()[1]
+    cand = _st.candidates
+    diag = list(_st.diag)
     clocks = clk.summary()
     if dist:
         t = torch.tensor([ms_step], device=dev)
@@ -359,6 +361,7 @@ def main():
                            "sample_prec": "f32" if prec == 1 else "f64",
                            "l2": "256 MiB buffer written between timed steps",
                            "rechecks_per_step": rech,
+                           "uncertified_by_cause": diag if form == B.FORM_TC_RECHECK else None,
                            "router": router_info,
                            "candidates_per_search": (cand / (2 * units)) if router else None},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,

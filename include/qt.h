@@ -149,6 +149,9 @@ typedef struct {
     int32_t form_used;      /* QT_FORM_* actually run                                 */
     int32_t device_status;  /* qt_status reported by the kernels                      */
     double ms;              /* device time of the forward step, if measured, else 0   */
+    int64_t diag[3];        /* tensor-core form: uncertified picks by cause (FP32 bound
+                               inside the two best chunks, tensor-core bound outside,
+                               index or FP16 range)                                    */
 } qt_stats;
 
 /* Context: one per device.  device = CUDA ordinal.  Not thread safe; use one

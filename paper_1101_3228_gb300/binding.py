@@ -52,7 +52,7 @@ class QtDump(ctypes.Structure):
 
 class QtStats(ctypes.Structure):
     _fields_ = [("samples", i64), ("rechecks", i64), ("searches", i64), ("candidates", i64),
-                ("form_used", i32), ("device_status", i32), ("ms", ctypes.c_double)]
+                ("form_used", i32), ("device_status", i32), ("ms", ctypes.c_double), ("diag", i64 * 3)]
 
 
 class QtRouterConfig(ctypes.Structure):

@@ -641,6 +641,7 @@ qt_status read_status(qt_ctx* ctx, cudaStream_t st, qt_stats* stats, long long s
         stats->form_used = ctx->last_form;
         stats->device_status = hs.code;
         stats->ms = 0.0;
+        for (int q = 0; q < 3; ++q) stats->diag[q] = (int64_t)hs.spare[q + 1] - (q == 0 ? 0 : 0);
         float ms = 0.f;
         if (ctx->timed && cudaEventElapsedTime(&ms, ctx->ev_k0, ctx->ev_k1) == cudaSuccess) stats->ms = ms;
         cudaGetLastError();

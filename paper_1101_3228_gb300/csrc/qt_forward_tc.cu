@@ -139,7 +139,7 @@ __device__ __forceinline__ void cc_chunk(const float* __restrict__ recs, int chu
 // smallest other FP32 score there), tensor-core scores outside them (B2tc: the
 // smallest chunk minimum of the other chunks, FP32-score units).
 __device__ __forceinline__ bool tc_certified(int d, float A, float best, float S1, float B2tc, float r1,
-                                             float inv_sigma)
+                                             float inv_sigma, int& why)
 {
     const float Ap = A * (1.0f + 0x1p-18f);
     const float r1p = r1 * (1.0f + 0x1p-18f);
@@ -151,9 +151,12 @@ __device__ __forceinline__ bool tc_certified(int d, float A, float best, float S
     const float rho = Ap + __fsqrt_rn(rad);
     const float lo_in = S1 - cc_bound(d, Ap, rho);
     const float lo_out = B2tc - tc_bound(d, Ap, rho, inv_sigma);
-    const float lhs = fminf(lo_in, lo_out), rhs = U + eta;
+    const float rhs = U + eta;
     // additive slack for the FP32 evaluation of both sides
-    return lhs - rhs > 0x1p-20f * (fabsf(lhs) + fabsf(rhs)) + eta;
+    const bool ok_in = lo_in - rhs > 0x1p-20f * (fabsf(lo_in) + fabsf(rhs)) + eta || lo_in == __int_as_float(0x7F800000);
+    const bool ok_out = lo_out - rhs > 0x1p-20f * (fabsf(lo_out) + fabsf(rhs)) + eta || lo_out == __int_as_float(0x7F800000);
+    why = ok_in ? (ok_out ? 0 : 2) : 1;
+    return ok_in && ok_out;
 }
 
 }  // namespace
@@ -453,8 +456,11 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
                     in2 = fminf(S1, best2);
                 }
                 const float B3cc = B3 * inv_sg * inv_sg;
-                const bool cert = tc_certified(d, isA ? cs.Aa : cs.Ab, best, in2, B3cc, r1, inv_sg) &&
-                                  idx < (isA ? L.NA : L.NB) && !(isA ? bigA : bigB);
+                int why = 0;
+                const bool tcok = tc_certified(d, isA ? cs.Aa : cs.Ab, best, in2, B3cc, r1, inv_sg, why);
+                const bool rng_ok = idx < (isA ? L.NA : L.NB) && !(isA ? bigA : bigB);
+                const bool cert = tcok && rng_ok;
+                if (valid && !cert) atomicAdd(&p.status->spare[!rng_ok ? 3 : why], 1ull);
                 if (isA) {
                     ci = idx;
                     needA = !cert && valid;

@@ -19,7 +19,7 @@ struct DevStatus {
     unsigned long long rechecks;   // FP64 re-evaluations
     unsigned long long candidates; // candidate distances (router form)
     unsigned long long done_items; // work items finished
-    unsigned long long spare[3];
+    unsigned long long spare[4];   // [0]: router grid checksum; [1..3]: diagnostics
 };
 
 // One layer pair (k, k+1) of the forward step.
