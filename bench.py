@@ -85,6 +85,26 @@ def flops_per_sample_layer(model):
     return float(cand * (2 * model.d + 1))
 
 
+def replica_seed(model, rank: int) -> int:
+    """Every rank runs an independent replica (weak scaling): its own Philox key."""
+    return int(model.seed) + 7919 * int(rank)
+
+
+def max_over_ranks(ms: float, dist, device=None) -> float:
+    """The slowest rank's time; the whole job waits for it."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, units_per_rank: int, ms: float) -> float:
+    """Whole-job throughput: the sample.layers of all ranks over the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def source_hash():
     h = hashlib.sha256()
     for d in ("paper_1101_3228_gb300/csrc", "include"):
@@ -235,7 +255,7 @@ def main():
     dev = torch.device("cuda", local)
     ctx = B.Context(local)
     stream = torch.cuda.current_stream()
-    seed = model.seed + 7919 * rank          # independent replica per rank
+    seed = replica_seed(model, rank)          # independent replica per rank
     grids = ctx.build_grids(model, grid_method(model), samples=max(20 * int(np.max(model.N)), 200000),
                             iters=20, seed=W.GRID_SEED_BASE + W.CONFIG_INDEX[model.name])
     form = {"auto": B.FORM_AUTO, "plain_f64": B.FORM_PLAIN_F64, "f32_recheck": B.FORM_F32_RECHECK,
@@ -295,11 +315,8 @@ def main():
     cand = _st.candidates
     diag = list(_st.diag)
     clocks = clk.summary()
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * units / (ms_step / 1e3)
+    ms_step = max_over_ranks(ms_step, dist, dev) if dist else ms_step
+    value = job_value(world, units, ms_step)
 
     # plain GPU comparator (exact FP64 brute force for d <= 2)
     plain = None
