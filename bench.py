@@ -67,7 +67,9 @@ def grid_method(model):
 
 
 def default_form(model, B):
-    return B.FORM_PLAIN_F64 if model.name == "bs1d" else B.FORM_F32_RECHECK
+    # the fastest certified form measured for each dimension class: the FP32 screen
+    # (exact through its certificate) up to d = 8, the tensor-core screen for d = 10
+    return B.FORM_TC_RECHECK if model.d >= 10 else B.FORM_F32_RECHECK
 
 
 def plain_form(model, B):
@@ -370,7 +372,8 @@ def main():
     if rank == 0:
         line = {"metric": "certified sample*layers/s (exact counts)", "value": value, "unit": "sample*layers/s",
                 "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {B.FORM_PLAIN_F64: "f64", B.FORM_TC_RECHECK: "f16x3+f32"}.get(form, "f32"),
                 "data": "synthetic",
                 "config": {"workload": model.name, "d": model.d, "n": model.n, "N": int(model.N[-1]),
                            "M": model.M, "form": B.FORM_NAMES[form],

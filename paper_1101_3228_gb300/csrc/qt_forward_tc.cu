@@ -211,7 +211,7 @@ __global__ void prep_tc_tiles_kernel(const float* __restrict__ rec32, GridInfo* 
 }
 
 template <int DM, int KT>
-__global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams p)
+__global__ void __launch_bounds__(256, 1) forward_tc_kernel(const ForwardParams p)
 {
     constexpr int K = 16 * KT;
     constexpr int kTileBytes = kTcTileN * K * 2;
@@ -226,6 +226,8 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
     __shared__ __align__(16) float s_pf[param_count(DM)];
     __shared__ __align__(16) double s_pd[param_count(DM)];
     __shared__ int s_abort;
+    __shared__ float s_mB1[kTcTileM], s_mBs[kTcTileM], s_mB3[kTcTileM];   // half-tile hand-over
+    __shared__ int s_mbc[kTcTileM], s_mbcs[kTcTileM];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -314,54 +316,55 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
         }
         bool loaded_now = !resident || new_layer;    // barriers of this item's tiles still to be waited
 
-        // ---- one sample per thread: draw, centre, write both operand rows
+        // ---- two warpgroups per sample row t: warpgroup 0 owns grid A (writes its
+        // operand row, reads accumulator columns 0-127, resolves and rechecks the
+        // A search), warpgroup 1 owns grid B (columns 128-255); both draw sample t
+        const int wg = tid >> 7;
+        const int t = tid & 127;
         const unsigned long long mtile = (unsigned long long)(item - L.item_begin) * kTcTileM;
-        const unsigned long long ms = mtile + (unsigned long long)tid;
+        const unsigned long long ms = mtile + (unsigned long long)t;
         const bool valid = ms < p.M;
         const Centred<DM> cs = centred_sample<DM>(p, s_pf, s_pd, s_GA.mu, s_GB.mu, k, valid ? ms : mtile);
-        bool bigA = false, bigB = false;   // outside the FP16 range: skip the screen, search exactly
+        float xown[DM];   // -2 (sample - mu) for this warpgroup's grid
+#pragma unroll
+        for (int l = 0; l < DM; ++l) xown[l] = wg == 0 ? cs.xa[l] : cs.yb[l];
+        const float Aown = wg == 0 ? cs.Aa : cs.Ab;
+        const GridInfo& Gown = wg == 0 ? s_GA : s_GB;
+        bool big = false;     // outside the FP16 range: skip the screen, search exactly
         {
-            const float sgA = ldexpf(1.0f, s_GA.tc_exp), sgB = ldexpf(1.0f, s_GB.tc_exp);
+            const float sg = ldexpf(1.0f, Gown.tc_exp);
+            unsigned char* base = sA + wg * kAbytes;
 #pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                unsigned char* base = sA + g * kAbytes;
-                // zero the row, then scatter [a_hi, a_hi, a_lo, 1, 1] into its K columns
+            for (int kb = 0; kb < K / 8; ++kb)
+                *reinterpret_cast<uint4*>(base + (((t >> 3) * (K / 8) + kb) * 64 + (t & 7) * 8) * 2) =
+                    make_uint4(0u, 0u, 0u, 0u);
+            __half* hrow = reinterpret_cast<__half*>(base);
+            auto at = [&](int q) -> __half& { return hrow[((t >> 3) * (K / 8) + (q >> 3)) * 64 + (t & 7) * 8 + (q & 7)]; };
 #pragma unroll
-                for (int kb = 0; kb < K / 8; ++kb)
-                    *reinterpret_cast<uint4*>(base + (((tid >> 3) * (K / 8) + kb) * 64 + (tid & 7) * 8) * 2) =
-                        make_uint4(0u, 0u, 0u, 0u);
-                __half* hrow = reinterpret_cast<__half*>(base);
-                auto at = [&](int q) -> __half& { return hrow[((tid >> 3) * (K / 8) + (q >> 3)) * 64 + (tid & 7) * 8 + (q & 7)]; };
-                bool big = false;
+            for (int l = 0; l < DM; ++l) big = big || !(fabsf(sg * xown[l]) <= 16384.0f);
 #pragma unroll
-                for (int l = 0; l < DM; ++l) {
-                    const float v = (g == 0 ? sgA * cs.xa[l] : sgB * cs.yb[l]);
-                    big = big || !(fabsf(v) <= 16384.0f);
+            for (int l = 0; l < DM; ++l) {
+                if (l < d) {
+                    const float v = big ? 0.0f : sg * xown[l];
+                    const __half h = __float2half_rn(v);
+                    at(l) = h;
+                    at(d + l) = h;
+                    at(2 * d + l) = __float2half_rn(v - __half2float(h));
                 }
-#pragma unroll
-                for (int l = 0; l < DM; ++l) {
-                    if (l < d) {
-                        const float v = big ? 0.0f : (g == 0 ? sgA * cs.xa[l] : sgB * cs.yb[l]);
-                        const __half h = __float2half_rn(v);
-                        at(l) = h;
-                        at(d + l) = h;
-                        at(2 * d + l) = __float2half_rn(v - __half2float(h));
-                    }
-                }
-                at(3 * d) = __float2half_rn(1.0f);
-                at(3 * d + 1) = __float2half_rn(1.0f);
-                if (g == 0) bigA = big; else bigB = big;
             }
+            at(3 * d) = __float2half_rn(1.0f);
+            at(3 * d + 1) = __float2half_rn(1.0f);
         }
         fence_proxy_async();     // generic-proxy writes of the operand rows -> tensor core
         __syncthreads();
 
         // ---- walk the tiles: MMA of tile i+1 overlaps the epilogue of tile i
-        // per sample: best chunk (B1, bc), second chunk (Bs, bcs), smallest other chunk minimum B3
+        // per sample and half tile: best chunk (B1, bc), second chunk (Bs, bcs),
+        // smallest other chunk minimum B3
         float B1 = __int_as_float(0x7F800000), Bs = __int_as_float(0x7F800000), B3 = __int_as_float(0x7F800000);
         int bc = 0, bcs = 1;
-        int ci = -1, cj = -1;
-        bool needA = false, needB = false;
+        int cown = -1;             // this warpgroup's cell for sample t
+        bool need = false;
         auto issue = [&](int i) {
             // thread 0 only: wait for the tile, then the MMA into accumulator i & 1
             const int slot = resident ? i : i % RS;
@@ -401,17 +404,25 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
             }
             mphase ^= (1u << (i & 1));
             tc_fence_after();
-            // epilogue: this thread's row, 256 scores in 16 chunks
+            // epilogue: this thread's row, its warpgroup's 128 columns, 8 chunks
             const int lt = i < tA ? i : i - tA;
 #pragma unroll
-            for (int q = 0; q < kTcTileN / 32; ++q) {
-                float v[32];
-                tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((i & 1) * kTcTileN + q * 32), v);
+            for (int q = 0; q < kTcTileN / 64; q += 2) {
+                float v[64];
+                tc_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                            (uint32_t)((i & 1) * kTcTileN + wg * (kTcTileN / 2) + q * 32),
+                        *reinterpret_cast<float(*)[32]>(v));
+                tc_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                            (uint32_t)((i & 1) * kTcTileN + wg * (kTcTileN / 2) + (q + 1) * 32),
+                        *reinterpret_cast<float(*)[32]>(v + 32));
                 tc_wait_ld();
+                float mcs[4];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float mc = min16(v + 16 * h);
-                    const int c = lt * (kTcTileN / kChunk) + q * 2 + h;
+                for (int h = 0; h < 4; ++h) mcs[h] = min16(v + 16 * h);
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const float mc = mcs[h];
+                    const int c = lt * (kTcTileN / kChunk) + wg * (kTcTileN / 2 / kChunk) + q * 2 + h;
                     const bool t1 = mc < B1, t2 = mc < Bs;
                     B3 = fminf(B3, fmaxf(mc, Bs));
                     Bs = fminf(Bs, fmaxf(mc, B1));
@@ -420,32 +431,55 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
                     bc = t1 ? c : bc;
                 }
             }
+            const bool endA = i == tA - 1, endB = i == nT - 1;
+            // the partner warpgroup hands its half-tile state to the owner of this grid
+            if ((endA && wg == 1) || (endB && wg == 0)) {
+                s_mB1[t] = B1;
+                s_mBs[t] = Bs;
+                s_mB3[t] = B3;
+                s_mbc[t] = bc;
+                s_mbcs[t] = bcs;
+            }
             tc_fence_before();
-            __syncthreads();      // accumulator i & 1 and (streamed) slot of tile i are free
+            __syncthreads();      // accumulator i & 1, (streamed) slot of tile i and the hand-over are ready
             if (tid == 0 && !resident && i + RS < nT) {
                 const uint32_t b = smem_u32(&s_bfull[slot]);
                 fence_proxy_async();
                 mbar_arrive_expect_tx(b, kTileBytes);
                 bulk_g2s(sB_u + slot * kTileBytes, tile_src(i + RS), kTileBytes, b);
             }
-            if (i == tA - 1 || i == nT - 1) {
-                // grid done: re-score the two best chunks in FP32 and certify
-                const bool isA = i == tA - 1;
-                const GridInfo& G = isA ? s_GA : s_GB;
-                const float inv_sg = ldexpf(1.0f, -G.tc_exp);
-                const float* recs = p.rec32 + G.roff * Rec32<DM>::kFloats;
-                const int nch = G.Npad / kChunk;      // chunks with FP32 records
+            if ((endA && wg == 0) || (endB && wg == 1)) {
+                // merge the two half-tile states: the two smallest chunk minima
+                // (ties to the lower chunk), the rest into B3
+                float v4[4] = {B1, Bs, s_mB1[t], s_mBs[t]};
+                int c4[4] = {bc, bcs, s_mbc[t], s_mbcs[t]};
+                float rest = fminf(B3, s_mB3[t]);
+                int f = 0;
+#pragma unroll
+                for (int q = 1; q < 4; ++q)
+                    if (v4[q] < v4[f] || (v4[q] == v4[f] && c4[q] < c4[f])) f = q;
+                int g2 = f == 0 ? 1 : 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q != f && (v4[q] < v4[g2] || (v4[q] == v4[g2] && c4[q] < c4[g2]))) g2 = q;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q != f && q != g2) rest = fminf(rest, v4[q]);
+                const int mbc = c4[f], mbcs = c4[g2];
+                // re-score the two best chunks in FP32 and certify
+                const float inv_sg = ldexpf(1.0f, -Gown.tc_exp);
+                const float* recs = p.rec32 + Gown.roff * Rec32<DM>::kFloats;
+                const int nch = Gown.Npad / kChunk;      // chunks with FP32 records
                 int idx, idx2;
                 float best, S1, r1, best2, S12, r12;
-                cc_chunk<DM>(recs, bc, isA ? cs.xa : cs.yb, idx, best, S1, r1);
-                if (bcs < nch && bcs != bc) {
-                    cc_chunk<DM>(recs, bcs, isA ? cs.xa : cs.yb, idx2, best2, S12, r12);
+                cc_chunk<DM>(recs, mbc, xown, idx, best, S1, r1);
+                if (mbcs < nch && mbcs != mbc) {
+                    cc_chunk<DM>(recs, mbcs, xown, idx2, best2, S12, r12);
                 } else {
                     idx2 = idx;
                     best2 = S12 = __int_as_float(0x7F800000);
                     r12 = r1;
                 }
-                // merge the two chunks: lowest index among equal bests
                 float in2;
                 if (best2 < best || (best2 == best && idx2 < idx)) {
                     in2 = fminf(S12, best);
@@ -455,19 +489,16 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
                 } else {
                     in2 = fminf(S1, best2);
                 }
-                const float B3cc = B3 * inv_sg * inv_sg;
+                const float B3cc = rest * inv_sg * inv_sg;
                 int why = 0;
-                const bool tcok = tc_certified(d, isA ? cs.Aa : cs.Ab, best, in2, B3cc, r1, inv_sg, why);
-                const bool rng_ok = idx < (isA ? L.NA : L.NB) && !(isA ? bigA : bigB);
+                const bool tcok = tc_certified(d, Aown, best, in2, B3cc, r1, inv_sg, why);
+                const bool rng_ok = idx < Gown.N && !big;
                 const bool cert = tcok && rng_ok;
                 if (valid && !cert) atomicAdd(&p.status->spare[!rng_ok ? 3 : why], 1ull);
-                if (isA) {
-                    ci = idx;
-                    needA = !cert && valid;
-                } else {
-                    cj = idx;
-                    needB = !cert && valid;
-                }
+                cown = idx;
+                need = !cert && valid;
+            }
+            if (endA || endB) {
                 B1 = Bs = B3 = __int_as_float(0x7F800000);
                 bc = 0;
                 bcs = 1;
@@ -484,29 +515,26 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
         if (resident) loaded_now = false;
         if (s_abort) break;
 
-        // ---- uncertified searches: warp FP32 re-screen, then the exact FP64 search
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            const bool need = g == 0 ? needA : needB;
+        // ---- uncertified searches of this warpgroup's grid: exact window search
+        {
             unsigned mask = __ballot_sync(0xFFFFFFFFu, need);
-            const GridInfo& G = g == 0 ? s_GA : s_GB;
             while (mask) {
                 const int src = __ffs(mask) - 1;
                 mask &= mask - 1;
                 double z[DM];
-                if (lane == src) exact_sample<DM>(p, s_pf, s_pd, k, ms, g == 1, z);
-                const int r = warp_window_nn<DM>(g == 0 ? cs.xa : cs.yb, g == 0 ? cs.Aa : cs.Ab, z, src,
-                                                 p.rec32 + G.roff * Rec32<DM>::kFloats, G.Npad,
-                                                 p.g64 + G.goff * d, G.N, d);
-                if (lane == src) {
-                    if (g == 0) ci = r; else cj = r;
-                }
+                if (lane == src) exact_sample<DM>(p, s_pf, s_pd, k, ms, wg == 1, z);
+                const int r = warp_window_nn<DM>(xown, Aown, z, src, p.rec32 + Gown.roff * Rec32<DM>::kFloats,
+                                                 Gown.Npad, p.g64 + Gown.goff * d, Gown.N, d);
+                if (lane == src) cown = r;
                 if (lane == 0) atomicAdd(&p.status->rechecks, 1ull);
             }
         }
+        if (wg == 1) s_mbc[t] = cown;     // hand cell j to warpgroup 0
+        __syncthreads();
 
         // ---- counters p^k_ij
-        if (valid) {
+        if (wg == 0 && valid) {
+            const int ci = cown, cj = s_mbc[t];
             if ((unsigned)ci >= (unsigned)L.NA || (unsigned)cj >= (unsigned)L.NB) {
                 record_error(p.status, 6 /* QT_EDEVICE */, 13);
             } else {
@@ -516,9 +544,9 @@ __global__ void __launch_bounds__(128, 1) forward_tc_kernel(const ForwardParams 
                     p.cellsB[ms] = cj;
                 }
                 if (p.dump_count > 0 && (ms % (unsigned long long)p.dump_stride) == 0ull) {
-                    const unsigned long long t = ms / (unsigned long long)p.dump_stride;
-                    if (t < (unsigned long long)p.dump_count) {
-                        const long long row = (long long)k * p.dump_count + (long long)t;
+                    const unsigned long long tt = ms / (unsigned long long)p.dump_stride;
+                    if (tt < (unsigned long long)p.dump_count) {
+                        const long long row = (long long)k * p.dump_count + (long long)tt;
                         double zx[DM], zy[DM];
                         exact_sample<DM>(p, s_pf, s_pd, k, ms, false, zx);
                         exact_sample<DM>(p, s_pf, s_pd, k, ms, true, zy);
@@ -553,13 +581,13 @@ static cudaError_t launch_tc(const ForwardParams& p, int dyn, int num_sms, int* 
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
     int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 128, dyn);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 256, dyn);
     if (e != cudaSuccess) return e;
     if (b != 1) return cudaErrorInvalidConfiguration;   // one CTA per SM: it owns all 512 TMEM columns
     *bps = b;
     long long grid = (long long)num_sms * b;
     if (grid > p.total_items) grid = p.total_items;
-    kern<<<(unsigned)grid, 128, dyn, st>>>(p);
+    kern<<<(unsigned)grid, 256, dyn, st>>>(p);
     return cudaGetLastError();
 }
 
