@@ -208,10 +208,12 @@ struct Centred {
     float Aa, Ab;          // |X - mu_A|, |Y - mu_B| of the rounded centred values
 };
 
-// Draw (or load) sample m and centre it on the two grids.
+// Draw (or load) sample m and centre it on the two grids (inlined form, for
+// kernels that draw one sample per thread).
 template <int DM>
-__device__ __noinline__ Centred<DM> centred_sample(const ForwardParams& p, const float* spf, const double* spd,
-                                                   const float* muA, const float* muB, int k, unsigned long long m)
+__device__ __forceinline__ Centred<DM> centred_sample_inl(const ForwardParams& p, const float* spf, const double* spd,
+                                                          const float* muA, const float* muB, int k,
+                                                          unsigned long long m)
 {
     Centred<DM> c;
     const int d = p.d;
@@ -252,6 +254,14 @@ __device__ __noinline__ Centred<DM> centred_sample(const ForwardParams& p, const
     c.Aa = __fsqrt_rn(na);
     c.Ab = __fsqrt_rn(nb);
     return c;
+}
+
+// Out-of-line form, for kernels that draw several samples per thread.
+template <int DM>
+__device__ __noinline__ Centred<DM> centred_sample(const ForwardParams& p, const float* spf, const double* spd,
+                                                   const float* muA, const float* muB, int k, unsigned long long m)
+{
+    return centred_sample_inl<DM>(p, spf, spd, muA, muB, k, m);
 }
 
 // Exact FP64 pair for the plain form.

@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(256, 1) forward_tc_kernel(const ForwardParams 
         const unsigned long long mtile = (unsigned long long)(item - L.item_begin) * kTcTileM;
         const unsigned long long ms = mtile + (unsigned long long)t;
         const bool valid = ms < p.M;
-        const Centred<DM> cs = centred_sample<DM>(p, s_pf, s_pd, s_GA.mu, s_GB.mu, k, valid ? ms : mtile);
+        const Centred<DM> cs = centred_sample_inl<DM>(p, s_pf, s_pd, s_GA.mu, s_GB.mu, k, valid ? ms : mtile);
         float xown[DM];   // -2 (sample - mu) for this warpgroup's grid
 #pragma unroll
         for (int l = 0; l < DM; ++l) xown[l] = wg == 0 ? cs.xa[l] : cs.yb[l];
@@ -408,17 +408,15 @@ __global__ void __launch_bounds__(256, 1) forward_tc_kernel(const ForwardParams 
             const int lt = i < tA ? i : i - tA;
 #pragma unroll
             for (int q = 0; q < kTcTileN / 64; q += 2) {
-                float v[64];
+                float va[32], vb[32];
                 tc_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
                             (uint32_t)((i & 1) * kTcTileN + wg * (kTcTileN / 2) + q * 32),
-                        *reinterpret_cast<float(*)[32]>(v));
+                        va);
                 tc_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
                             (uint32_t)((i & 1) * kTcTileN + wg * (kTcTileN / 2) + (q + 1) * 32),
-                        *reinterpret_cast<float(*)[32]>(v + 32));
+                        vb);
                 tc_wait_ld();
-                float mcs[4];
-#pragma unroll
-                for (int h = 0; h < 4; ++h) mcs[h] = min16(v + 16 * h);
+                const float mcs[4] = {min16(va), min16(va + 16), min16(vb), min16(vb + 16)};
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     const float mc = mcs[h];
