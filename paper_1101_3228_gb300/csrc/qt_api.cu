@@ -27,7 +27,7 @@ __global__ void kmeans_assign_kernel(int, long long, const float*, int, const fl
                                      unsigned long long*, int);
 __global__ void kmeans_update_kernel(int, int, const unsigned long long*, const unsigned long long*, float*);
 __global__ void map_grid_kernel(int, int, const double*, const double*, const double*, double*);
-__global__ void prep_tc_tiles_kernel(const float*, GridInfo*, int, int, int, int, long long, __half*);
+__global__ void prep_tc_tiles_kernel(const float*, GridInfo*, int, int, int, int, int, long long, __half*);
 cudaError_t launch_router_forward(int dm, const ForwardParams& p, int num_sms, int* bps, cudaStream_t st);
 cudaError_t launch_grid_checksum(const double* grids, long long count, unsigned long long* out, cudaStream_t st);
 void router_fill_params(const qt_router* r, ForwardParams& fp);
@@ -404,19 +404,22 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
         return QT_OK;
     }
     if (P.form == kTcRecheck) {
-        // one CTA of 128 threads per SM owns the 512 TMEM columns (two 256-column
-        // accumulators); operand tiles in a ring of 128 KB, which also keeps the
-        // shared memory above half of the SM so that no second CTA fits
+        // one CTA of 13 warps per SM owns the 512 TMEM columns (two 256-column
+        // accumulators); the operand tiles take what the pipeline's buffers
+        // leave of the shared memory, at most 16 tiles
         P.tc_k = P.dm <= 4 ? 16 : 32;
         const size_t tile_bytes = (size_t)kTcTileN * P.tc_k * 2;
-        P.tc_slots = (int)std::min<size_t>(16, (128 * 1024) / tile_bytes);
+        const long long fixed = tc_fixed_smem(P.dm, P.tc_k);
+        const long long room = (long long)ctx->smem_optin - fixed - 2048;
+        P.tc_slots = (int)std::min<long long>(kTcMaxSlots, room > 0 ? room / (long long)tile_bytes : 0);
+        if (P.tc_slots < 2) return fail(ctx, QT_EUNSUPPORTED, "too little shared memory for the tensor-core form");
         int tmax = 0;
         for (int k = 0; k < n; ++k) tmax = std::max(tmax, P.grids[k].tc_tiles + P.grids[k + 1].tc_tiles);
         P.tc_resident = tmax <= P.tc_slots;
         P.S = 1;
-        P.block = 128;
+        P.block = kTcThreads;
         P.tile = kTcTileM;
-        P.grid_bytes = 2 * (size_t)kTcTileM * P.tc_k * 2 + (size_t)P.tc_slots * tile_bytes;
+        P.grid_bytes = (size_t)fixed + (size_t)P.tc_slots * tile_bytes;
         P.hist_bytes = 0;
         P.dyn_smem = P.grid_bytes;
         P.layers.resize(n);
@@ -559,7 +562,7 @@ qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long
     if (P.form == kTcRecheck) {
         const long long rows = P.tc_total_tiles * kTcTileN;
         prep_tc_tiles_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(
-            (const float*)drec32, (GridInfo*)dgrids, P.ngrids, P.d, P.rec_floats, P.tc_k, rows, (__half*)dtiles);
+            (const float*)drec32, (GridInfo*)dgrids, P.ngrids, P.d, P.dm, P.rec_floats, P.tc_k, rows, (__half*)dtiles);
         QT_CUDA(cudaGetLastError());
     }
     ForwardParams fp;

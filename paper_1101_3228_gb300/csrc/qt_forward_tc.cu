@@ -7,24 +7,32 @@
 // [a_hi, a_hi, a_lo, 1, 1] times grid rows [g_hi, g_lo, g_hi, cc_hi, cc_lo],
 // a = -2 sigma x^, g = sigma g^, cc = sigma^2 |g^|^2, each split into an FP16
 // head and an FP16 tail, sigma = 2^tc_exp so that the grid fits in [-1, 1].
-// The three cross products reproduce the FP32 score to about 2^-21 relative
-// (the tail x tail product is below 2^-22); K = 16 holds 3d + 2 columns for
-// d <= 4, K = 32 for d <= 10.
+// Each group of coordinates takes DM columns (the dimension class, zero
+// padded), so K = 16 holds 3 DM + 2 columns for DM <= 4 and K = 32 for
+// DM <= 10.  The three cross products reproduce the FP32 score to about
+// 2^-21 relative (the tail x tail product is below 2^-22).
 //
-// Per work item (layer k, 128 samples): one thread per sample draws the pair,
-// writes both sample rows into shared memory, and the CTA walks the operand
-// tiles of Gamma_k and Gamma_{k+1}: thread 0 issues the MMA of tile t + 1 into
-// one of two 256-column TMEM accumulators while all 128 threads read tile t
-// with tcgen05.ld and keep, per sample, the running minimum per 16-column chunk
-// (best, smallest other chunk minimum, best chunk).  Operand tiles arrive by
-// bulk copies (TMA engine); they stay in shared memory for the whole layer when
-// both grids fit, else they stream through a ring.
+// A CTA is one persistent pipeline over its work items (layer k, 128 samples)
+// with three roles that meet only at mbarriers:
+//   producer warp    -- bulk copies of the grids' operand tiles (kept for the
+//                       whole layer when both grids fit, else streamed
+//                       through a ring) and the MMAs, one elected thread;
+//   two epilogue     -- warpgroup b reads accumulator b (tiles alternate
+//   warpgroups          between the two 256-column TMEM accumulators) with
+//                       tcgen05.ld and keeps, per sample, the two best
+//                       16-column chunks and the smallest other chunk minimum;
+//   four certifier   -- draw the samples of the next item (operand rows and
+//   warps               centred FP32 coordinates), then merge the two
+//                       warpgroups' chunk states of this item, certify,
+//                       recheck and count.
+// While the tensor cores work on item n, the certifiers draw item n + 1 and
+// certify item n - 1's results as they arrive.
 //
-// Exactness: the best chunk is re-scored on the CUDA cores in FP32 (index and
-// second score inside the chunk), and the pick is certified against the exact
-// FP64 distance with the FP32 bound inside the chunk and the tensor-core bound
-// outside it; uncertified samples get a warp-wide FP32 re-screen of the whole
-// grid and, if that cannot certify either, the exact FP64 search.
+// Exactness: the two best chunks are re-scored on the CUDA cores in FP32, and
+// the pick is certified against the exact FP64 distance with the FP32 bound
+// inside those chunks and the tensor-core bound outside them; uncertified
+// samples go to the exact window search (FP32 screen of the whole grid, exact
+// FP64 distances inside the certified window).
 #include <cuda_fp16.h>
 
 #include "qt_forward.cuh"
@@ -105,30 +113,46 @@ __device__ __forceinline__ float cc_bound(int d, float A, float r)
 
 // FP32 scores of one 16-record chunk of a grid (records in global memory):
 // lowest-index minimum, the smallest other score, the norm of the best record.
+// All 16 records are loaded before any of them is compared, so that their
+// loads are in flight together.
 template <int DM>
 __device__ __forceinline__ void cc_chunk(const float* __restrict__ recs, int chunk, const float (&x)[DM], int& idx,
                                          float& best, float& S1, float& r1)
 {
     constexpr int F = Rec32<DM>::kFloats;
-    idx = -1;
-    best = __int_as_float(0x7F800000);
+    constexpr int V = F / 4;
+    const float4* r4 = reinterpret_cast<const float4*>(recs) + (long long)chunk * kChunk * V;
+    float sc[kChunk];
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q) {
+        float4 a[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) a[v] = r4[q * V + v];
+        float f[4 * V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            f[4 * v] = a[v].x;
+            f[4 * v + 1] = a[v].y;
+            f[4 * v + 2] = a[v].z;
+            f[4 * v + 3] = a[v].w;
+        }
+        float s = f[0];
+#pragma unroll
+        for (int l = 0; l < DM; ++l) s = __fmaf_rn(x[l], f[1 + l], s);
+        sc[q] = s;
+    }
+    best = sc[0];
     S1 = __int_as_float(0x7F800000);
     int bq = 0;
-    for (int q = 0; q < kChunk; ++q) {
-        const float* r = recs + (chunk * kChunk + q) * F;
-        float sc = r[0];
 #pragma unroll
-        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], r[1 + l], sc);
-        if (sc < best) {
-            S1 = fminf(S1, best);
-            best = sc;
-            bq = q;
-        } else {
-            S1 = fminf(S1, sc);
-        }
+    for (int q = 1; q < kChunk; ++q) {
+        const bool t = sc[q] < best;
+        S1 = fminf(S1, t ? best : sc[q]);
+        best = t ? sc[q] : best;
+        bq = t ? q : bq;
     }
     idx = chunk * kChunk + bq;
-    const float* r = recs + idx * F;
+    const float* r = recs + (long long)idx * F;
     float n2 = 0.0f;
 #pragma unroll
     for (int l = 0; l < DM; ++l) n2 = __fmaf_rn(r[1 + l], r[1 + l], n2);
@@ -159,13 +183,80 @@ __device__ __forceinline__ bool tc_certified(int d, float A, float best, float S
     return ok_in && ok_out;
 }
 
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait with one outcome for the whole warp (the epilogue's tcgen05.ld
+// and the certifiers' ballots need converged warps).
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, long long budget)
+{
+    const bool ok = mbar_wait_bounded(bar, parity, budget);
+    return __all_sync(0xFFFFFFFFu, ok);
+}
+
+__device__ __forceinline__ int layer_of(const ForwardParams& p, long long item)
+{
+    int lo = 0, hi = p.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.layers[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per sample, over the chunks a warpgroup has seen (in increasing order): the
+// best chunk minimum B1 (chunk bc), the second Bs (chunk bcs) and the smallest
+// of the others B3; ties keep the lower chunk.
+struct ChunkTrack {
+    float B1, Bs, B3;
+    int bc, bcs;
+    __device__ __forceinline__ void reset()
+    {
+        B1 = Bs = B3 = __int_as_float(0x7F800000);
+        bc = 0;
+        bcs = 1;
+    }
+    __device__ __forceinline__ void add(float mc, int c)
+    {
+        const bool t1 = mc < B1, t2 = mc < Bs;
+        B3 = fminf(B3, fmaxf(mc, Bs));
+        Bs = fminf(Bs, fmaxf(mc, B1));
+        bcs = t1 ? bc : (t2 ? c : bcs);
+        B1 = fminf(B1, mc);
+        bc = t1 ? c : bc;
+    }
+};
+
+__device__ __forceinline__ bool pair_less(float a, int ia, float b, int ib)
+{
+    return a < b || (a == b && ia < ib);
+}
+
+__device__ __forceinline__ void pair_sort2(float& a, int& ia, float& b, int& ib)
+{
+    if (pair_less(b, ib, a, ia)) {
+        const float v = a;
+        a = b;
+        b = v;
+        const int i = ia;
+        ia = ib;
+        ib = i;
+    }
+}
+
 }  // namespace
 
+
+
 // FP16 operand tiles of every grid: row j of grid g (tile j/256) holds
-// [g_hi (d), g_lo (d), g_hi (d), cc_hi, cc_lo, 0 ...] of sigma g^ and
-// sigma^2 cc; padded rows carry cc_hi = +inf.  Layout inside a tile: core
-// matrices of 8 rows x 8 halves, (row block, K block) at ((n/8)(K/8) + k/8) * 64.
-__global__ void prep_tc_tiles_kernel(const float* __restrict__ rec32, GridInfo* gi, int ngrids, int d,
+// [g_hi (dm), g_lo (dm), g_hi (dm), cc_hi, cc_lo, 0 ...] of sigma g^ and
+// sigma^2 cc (coordinates l >= d zero); padded rows carry cc_hi = +inf.
+// Layout inside a tile: core matrices of 8 rows x 8 halves, (row block,
+// K block) at ((n/8)(K/8) + k/8) * 64.
+__global__ void prep_tc_tiles_kernel(const float* __restrict__ rec32, GridInfo* gi, int ngrids, int d, int dm,
                                      int rec_floats, int K, long long total_rows, __half* tiles)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -198,52 +289,87 @@ __global__ void prep_tc_tiles_kernel(const float* __restrict__ rec32, GridInfo* 
             const __half h = __float2half_rn(v);
             const __half lo16 = __float2half_rn(v - __half2float(h));
             put(l, h);
-            put(d + l, lo16);
-            put(2 * d + l, h);
+            put(dm + l, lo16);
+            put(2 * dm + l, h);
         }
         const float c = sg * sg * rc[0];
         const __half ch = __float2half_rn(c);
-        put(3 * d, ch);
-        put(3 * d + 1, __float2half_rn(c - __half2float(ch)));
+        put(3 * dm, ch);
+        put(3 * dm + 1, __float2half_rn(c - __half2float(ch)));
     } else {
-        put(3 * d, __float2half_rn(__int_as_float(0x7F800000)));
+        put(3 * dm, __float2half_rn(__int_as_float(0x7F800000)));
     }
 }
 
+namespace {
+
+constexpr int kEpiWarps = 8;       // warps 0-7: epilogue warpgroups 0 and 1
+constexpr int kProducerWarp = 8;   // warp 8: operand tiles and MMAs
+constexpr int kCertWarp0 = 9;      // warps 9-12: draw, certify, recheck, count
+static_assert(kTcThreads == 13 * 32, "role layout");
+
+// What a certifier warp needs of the layer of an item (shared memory, one per
+// warp and operand slot, plus one for the layer of its draws).
+struct SlotLayer {
+    long long item_begin, coff, goffA, goffB, roffA, roffB;
+    int32_t k, NA, NB, NpadA, NpadB, expA, expB, spare;
+};
+
+}  // namespace
+
 template <int DM, int KT>
-__global__ void __launch_bounds__(256, 1) forward_tc_kernel(const ForwardParams p)
+__global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const ForwardParams p)
 {
     constexpr int K = 16 * KT;
+    static_assert(3 * DM + 2 <= K, "operand row");
     constexpr int kTileBytes = kTcTileN * K * 2;
-    constexpr int kAbytes = kTcTileM * K * 2;
+    constexpr int kOpBytes = kTcTileM * K * 2;
+    constexpr int PC = param_count(DM);
+    constexpr int PCpad = (PC + 1) / 2 * 2;
+    constexpr int F = Rec32<DM>::kFloats;
+    const float kInf = __int_as_float(0x7F800000);
     extern __shared__ __align__(128) unsigned char dsm_tc[];
-    __shared__ __align__(8) unsigned long long s_bfull[16];
-    __shared__ __align__(8) unsigned long long s_mma[2];
+    __shared__ __align__(8) unsigned long long s_tfull[kTcMaxSlots], s_tempty[kTcMaxSlots];
+    __shared__ __align__(8) unsigned long long s_accfull[2], s_accempty[2];
+    __shared__ __align__(8) unsigned long long s_opfull[2], s_opempty[2];
+    __shared__ __align__(8) unsigned long long s_stA[2], s_stB[2], s_stempty[2];
+    __shared__ __align__(8) unsigned long long s_drain;
     __shared__ uint32_t s_tmem;
-    __shared__ long long s_item;
-    __shared__ LayerDesc s_L;
-    __shared__ GridInfo s_GA, s_GB;
-    __shared__ __align__(16) float s_pf[param_count(DM)];
-    __shared__ __align__(16) double s_pd[param_count(DM)];
     __shared__ int s_abort;
-    __shared__ float s_mB1[kTcTileM], s_mBs[kTcTileM], s_mB3[kTcTileM];   // half-tile hand-over
-    __shared__ int s_mbc[kTcTileM], s_mbcs[kTcTileM];
+    __shared__ SlotLayer s_slot[4][3];
+    __shared__ float s_mu[4][2 * DM];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const int d = p.d;
     const int RS = p.tc_slots;
-    unsigned char* sA = dsm_tc;                     // two sample operands (grid A, grid B)
-    unsigned char* sB = dsm_tc + 2 * kAbytes;         // operand tile ring
-    const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
+    const long long G = gridDim.x;
+    // dynamic shared memory: [tile ring][sample operands][chunk states][centred samples][parameters]
+    unsigned char* ring = dsm_tc;
+    unsigned char* ops = ring + (size_t)RS * kTileBytes;                       // [item slot][grid] rows
+    float* sst = reinterpret_cast<float*>(ops + 4 * kOpBytes);                 // [slot][grid][wg][5][128]
+    float* scert = sst + 2 * 2 * 2 * 5 * kTcTileM;                             // [slot][grid][DM + 1][128]
+    double* sparam = reinterpret_cast<double*>(scert + 2 * 2 * (DM + 1) * kTcTileM);   // [cert warp][PCpad]
+    const uint32_t ring_u = smem_u32(ring), ops_u = smem_u32(ops);
 
     if (tid == 0) {
-        for (int t = 0; t < RS; ++t) mbar_init(smem_u32(&s_bfull[t]), 1);
-        mbar_init(smem_u32(&s_mma[0]), 1);
-        mbar_init(smem_u32(&s_mma[1]), 1);
-        fence_proxy_async();
+        for (int i = 0; i < kTcMaxSlots; ++i) {
+            mbar_init(smem_u32(&s_tfull[i]), 1);
+            mbar_init(smem_u32(&s_tempty[i]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&s_accfull[b]), 1);
+            mbar_init(smem_u32(&s_accempty[b]), 128);
+            mbar_init(smem_u32(&s_opfull[b]), 128);
+            mbar_init(smem_u32(&s_opempty[b]), 1);
+            mbar_init(smem_u32(&s_stA[b]), 256);
+            mbar_init(smem_u32(&s_stB[b]), 256);
+            mbar_init(smem_u32(&s_stempty[b]), 128);
+        }
+        mbar_init(smem_u32(&s_drain), 1);
         s_abort = 0;
+        fence_proxy_async();
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -255,313 +381,493 @@ __global__ void __launch_bounds__(256, 1) forward_tc_kernel(const ForwardParams 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
+    volatile int* abort_flag = &s_abort;
 
-    uint32_t bphase = 0;                   // bit t: parity of slot t's barrier
-    uint32_t mphase = 0;                   // bit b: parity of accumulator b's barrier
-    uint32_t idesc = (1u << 4) | ((uint32_t)(kTcTileN >> 3) << 17) | ((uint32_t)(kTcTileM >> 4) << 24);
-    int cur = -1;
-
-    while (true) {
-        if (tid == 0) {
-            long long it = -1;
-            if (*((volatile int32_t*)&p.status->code) == 0) it = (long long)atomicAdd(&p.status->queue, 1ull);
-            s_item = it;
-        }
-        __syncthreads();
-        const long long item = s_item;
-        if (item < 0 || item >= p.total_items) break;
-        int k = (cur >= 0 && item >= s_L.item_begin && item < s_L.item_begin + s_L.items) ? cur : -1;
-        if (k < 0) {
-            int lo = 0, hi = p.n - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (p.layers[mid].item_begin <= item) lo = mid; else hi = mid - 1;
-            }
-            k = lo;
-        }
-        const bool new_layer = k != cur;
-        if (new_layer) {
-            __syncthreads();
-            if (tid == 0) {
-                s_L = p.layers[k];
-                s_GA = p.grids[s_L.gridA];
-                s_GB = p.grids[s_L.gridB];
-            }
-            if (p.source == kSampler) {
-                const int pc = param_count(d);
-                for (int e = tid; e < pc; e += blockDim.x) {
-                    s_pf[e] = p.params_f[(long long)k * p.params_stride + e];
-                    s_pd[e] = p.params_d[(long long)k * p.params_stride + e];
+    if (warp == kProducerWarp) {
+        // ================================================================ producer
+        if (lane == 0) {
+            const bool resident = p.tc_resident != 0;
+            const unsigned char* tiles = reinterpret_cast<const unsigned char*>(p.tc_tiles);
+            const uint32_t idesc =
+                (1u << 4) | ((uint32_t)(kTcTileN >> 3) << 17) | ((uint32_t)(kTcTileM >> 4) << 24);
+            int cur = -1, tA = 0, nT = 0;
+            long long toffA = 0, toffB = 0, lbeg = 0, lend = 0;
+            uint32_t tph = 0, pend = 0, drains = 0;
+            long long qc = 0, ql = 0;          // streamed ring: positions consumed, loaded
+            long long ln = 0;                  // streamed ring: load cursor (item ordinal, tile)
+            int li = 0, ltA = 0, lnT = 0;
+            long long ltoffA = 0, ltoffB = 0, llbeg = 0, llend = 0;
+            auto fail = [&](int where) {
+                record_error(p.status, 4 /* QT_ETIMEOUT */, where);
+                *abort_flag = 1;
+            };
+            // streamed ring: issue the copies of the positions before `upto`
+            auto load_ahead = [&](long long upto) -> bool {
+                while (ql < upto) {
+                    const long long item = blockIdx.x + ln * G;
+                    if (item >= p.total_items) return true;
+                    if (li == 0 && (item < llbeg || item >= llend)) {
+                        const LayerDesc& L = p.layers[layer_of(p, item)];
+                        llbeg = L.item_begin;
+                        llend = llbeg + L.items;
+                        ltA = p.grids[L.gridA].tc_tiles;
+                        lnT = ltA + p.grids[L.gridB].tc_tiles;
+                        ltoffA = p.grids[L.gridA].tc_toff;
+                        ltoffB = p.grids[L.gridB].tc_toff;
+                    }
+                    const int r = (int)(ql % RS);
+                    if (!mbar_wait_bounded(smem_u32(&s_tempty[r]), (uint32_t)((ql / RS) & 1) ^ 1u, p.spin_budget))
+                        return false;
+                    const long long src = li < ltA ? ltoffA + li : ltoffB + (li - ltA);
+                    mbar_arrive_expect_tx(smem_u32(&s_tfull[r]), kTileBytes);
+                    bulk_g2s(ring_u + r * kTileBytes, tiles + src * kTileBytes, kTileBytes, smem_u32(&s_tfull[r]));
+                    ++ql;
+                    if (++li == lnT) {
+                        li = 0;
+                        ++ln;
+                    }
                 }
-            }
-            __syncthreads();
-            cur = k;
-        }
-        const LayerDesc& L = s_L;
-        const int tA = s_GA.tc_tiles, tB = s_GB.tc_tiles, nT = tA + tB;
-        const bool resident = p.tc_resident != 0;
-        auto tile_src = [&](int i) -> const unsigned char* {
-            const long long gt = i < tA ? s_GA.tc_toff + i : s_GB.tc_toff + (i - tA);
-            return reinterpret_cast<const unsigned char*>(p.tc_tiles) + gt * (long long)kTileBytes;
-        };
-        // ---- operand tiles: all of them once per layer (resident) or the first RS (streamed)
-        if (tid == 0 && (!resident || new_layer)) {
-            fence_proxy_async();
-            const int first = resident ? nT : min(RS, nT);
-            for (int i = 0; i < first; ++i) {
-                const uint32_t b = smem_u32(&s_bfull[i]);
-                mbar_arrive_expect_tx(b, kTileBytes);
-                bulk_g2s(sB_u + i * kTileBytes, tile_src(i), kTileBytes, b);
-            }
-        }
-        bool loaded_now = !resident || new_layer;    // barriers of this item's tiles still to be waited
-
-        // ---- two warpgroups per sample row t: warpgroup 0 owns grid A (writes its
-        // operand row, reads accumulator columns 0-127, resolves and rechecks the
-        // A search), warpgroup 1 owns grid B (columns 128-255); both draw sample t
-        const int wg = tid >> 7;
-        const int t = tid & 127;
-        const unsigned long long mtile = (unsigned long long)(item - L.item_begin) * kTcTileM;
-        const unsigned long long ms = mtile + (unsigned long long)t;
-        const bool valid = ms < p.M;
-        const Centred<DM> cs = centred_sample_inl<DM>(p, s_pf, s_pd, s_GA.mu, s_GB.mu, k, valid ? ms : mtile);
-        float xown[DM];   // -2 (sample - mu) for this warpgroup's grid
-#pragma unroll
-        for (int l = 0; l < DM; ++l) xown[l] = wg == 0 ? cs.xa[l] : cs.yb[l];
-        const float Aown = wg == 0 ? cs.Aa : cs.Ab;
-        const GridInfo& Gown = wg == 0 ? s_GA : s_GB;
-        bool big = false;     // outside the FP16 range: skip the screen, search exactly
-        {
-            const float sg = ldexpf(1.0f, Gown.tc_exp);
-            unsigned char* base = sA + wg * kAbytes;
-#pragma unroll
-            for (int kb = 0; kb < K / 8; ++kb)
-                *reinterpret_cast<uint4*>(base + (((t >> 3) * (K / 8) + kb) * 64 + (t & 7) * 8) * 2) =
-                    make_uint4(0u, 0u, 0u, 0u);
-            __half* hrow = reinterpret_cast<__half*>(base);
-            auto at = [&](int q) -> __half& { return hrow[((t >> 3) * (K / 8) + (q >> 3)) * 64 + (t & 7) * 8 + (q & 7)]; };
-#pragma unroll
-            for (int l = 0; l < DM; ++l) big = big || !(fabsf(sg * xown[l]) <= 16384.0f);
-#pragma unroll
-            for (int l = 0; l < DM; ++l) {
-                if (l < d) {
-                    const float v = big ? 0.0f : sg * xown[l];
-                    const __half h = __float2half_rn(v);
-                    at(l) = h;
-                    at(d + l) = h;
-                    at(2 * d + l) = __float2half_rn(v - __half2float(h));
+                return true;
+            };
+            bool ok = resident || load_ahead(RS - 1);
+            if (!ok) fail(20);
+            long long g = 0;                   // tiles issued so far: tile g goes to accumulator g & 1
+            for (long long n = 0; ok; ++n) {
+                const long long item = blockIdx.x + n * G;
+                if (item >= p.total_items || *abort_flag) break;
+                if (item < lbeg || item >= lend) {
+                    const int k = layer_of(p, item);
+                    const LayerDesc& L = p.layers[k];
+                    lbeg = L.item_begin;
+                    lend = lbeg + L.items;
+                    tA = p.grids[L.gridA].tc_tiles;
+                    nT = tA + p.grids[L.gridB].tc_tiles;
+                    toffA = p.grids[L.gridA].tc_toff;
+                    toffB = p.grids[L.gridB].tc_toff;
+                    if (resident) {
+                        if (cur >= 0) {
+                            // the previous layer's MMAs read the slots about to be overwritten
+                            tc_commit(smem_u32(&s_drain));
+                            if (!mbar_wait_bounded(smem_u32(&s_drain), drains & 1u, p.spin_budget)) {
+                                fail(21);
+                                break;
+                            }
+                            ++drains;
+                        }
+                        for (int i = 0; i < nT; ++i) {
+                            const long long src = i < tA ? toffA + i : toffB + (i - tA);
+                            mbar_arrive_expect_tx(smem_u32(&s_tfull[i]), kTileBytes);
+                            bulk_g2s(ring_u + i * kTileBytes, tiles + src * kTileBytes, kTileBytes,
+                                     smem_u32(&s_tfull[i]));
+                            pend |= 1u << i;
+                        }
+                    }
+                    cur = k;
                 }
-            }
-            at(3 * d) = __float2half_rn(1.0f);
-            at(3 * d + 1) = __float2half_rn(1.0f);
-        }
-        fence_proxy_async();     // generic-proxy writes of the operand rows -> tensor core
-        __syncthreads();
-
-        // ---- walk the tiles: MMA of tile i+1 overlaps the epilogue of tile i
-        // per sample and half tile: best chunk (B1, bc), second chunk (Bs, bcs),
-        // smallest other chunk minimum B3
-        float B1 = __int_as_float(0x7F800000), Bs = __int_as_float(0x7F800000), B3 = __int_as_float(0x7F800000);
-        int bc = 0, bcs = 1;
-        int cown = -1;             // this warpgroup's cell for sample t
-        bool need = false;
-        auto issue = [&](int i) {
-            // thread 0 only: wait for the tile, then the MMA into accumulator i & 1
-            const int slot = resident ? i : i % RS;
-            if (loaded_now || !resident) {
-                const uint32_t b = smem_u32(&s_bfull[slot]);
-                if (!mbar_wait_bounded(b, (bphase >> slot) & 1u, p.spin_budget)) {
-                    record_error(p.status, 4 /* QT_ETIMEOUT */, 11);
-                    s_abort = 1;
-                    mbar_wait_bounded(b, (bphase >> slot) & 1u, 1ll << 24);
+                const int os = (int)(n & 1);
+                if (!mbar_wait_bounded(smem_u32(&s_opfull[os]), (uint32_t)((n >> 1) & 1), p.spin_budget)) {
+                    fail(22);
+                    break;
                 }
+                for (int i = 0; i < nT; ++i) {
+                    const long long gg = g + i;
+                    const int b = (int)(gg & 1);
+                    if (!mbar_wait_bounded(smem_u32(&s_accempty[b]), (uint32_t)((gg >> 1) & 1) ^ 1u,
+                                           p.spin_budget)) {
+                        fail(23);
+                        ok = false;
+                        break;
+                    }
+                    int slot;
+                    if (resident) {
+                        slot = i;
+                        if ((pend >> i) & 1u) {
+                            if (!mbar_wait_bounded(smem_u32(&s_tfull[i]), (tph >> i) & 1u, p.spin_budget)) {
+                                fail(24);
+                                ok = false;
+                                break;
+                            }
+                            tph ^= 1u << i;
+                            pend &= ~(1u << i);
+                        }
+                    } else {
+                        slot = (int)(qc % RS);
+                        if (!mbar_wait_bounded(smem_u32(&s_tfull[slot]), (uint32_t)((qc / RS) & 1), p.spin_budget)) {
+                            fail(24);
+                            ok = false;
+                            break;
+                        }
+                    }
+                    tc_fence_after();
+                    const uint32_t a_base = ops_u + (uint32_t)((os * 2 + (i < tA ? 0 : 1)) * kOpBytes);
+                    const uint32_t b_base = ring_u + (uint32_t)(slot * kTileBytes);
+                    const uint32_t dt = tmem + (uint32_t)(b * kTcTileN);
+#pragma unroll
+                    for (int s = 0; s < KT; ++s) {
+                        const uint64_t ad = smem_desc(a_base + s * 256, 128, K * 16);
+                        const uint64_t bd = smem_desc(b_base + s * 256, 128, K * 16);
+                        tc_mma(dt, ad, bd, idesc, s > 0 ? 1u : 0u);
+                    }
+                    tc_commit(smem_u32(&s_accfull[b]));
+                    if (!resident) {
+                        tc_commit(smem_u32(&s_tempty[slot]));
+                        ++qc;
+                        if (!load_ahead(qc + RS - 1)) {
+                            fail(25);
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+                if (!ok) break;
+                tc_commit(smem_u32(&s_opempty[os]));
+                g += nT;
             }
+            // every MMA issued completes and every copy issued lands before the
+            // tensor memory and the shared memory are released
+            tc_commit(smem_u32(&s_drain));
+            mbar_wait_bounded(smem_u32(&s_drain), drains & 1u, 1ll << 24);
+            if (resident) {
+                for (int i = 0; i < kTcMaxSlots; ++i)
+                    if ((pend >> i) & 1u) mbar_wait_bounded(smem_u32(&s_tfull[i]), (tph >> i) & 1u, 1ll << 24);
+            } else {
+                for (long long q = qc; q < ql; ++q)
+                    mbar_wait_bounded(smem_u32(&s_tfull[q % RS]), (uint32_t)((q / RS) & 1), 1ll << 24);
+            }
+        }
+    } else if (warp < kEpiWarps) {
+        // ================================================================ epilogue
+        const int wg = warp >> 2;
+        const int t = (warp & 3) * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(wg * kTcTileN);
+        int tA = 0, nT = 0;
+        long long g = 0, lbeg = 0, lend = 0;
+        ChunkTrack tr;
+        auto process = [&](long long gg, int lt) -> bool {
+            if (!warp_wait(smem_u32(&s_accfull[wg]), (uint32_t)((gg >> 1) & 1), p.spin_budget)) return false;
             tc_fence_after();
-            const uint32_t a_base = sA_u + (i < tA ? 0 : kAbytes);
-            const uint32_t b_base = sB_u + slot * kTileBytes;
-            const uint32_t dt = tmem + (uint32_t)((i & 1) * kTcTileN);
 #pragma unroll
-            for (int s = 0; s < KT; ++s) {
-                const uint64_t ad = smem_desc(a_base + s * 256, 128, K * 16);
-                const uint64_t bd = smem_desc(b_base + s * 256, 128, K * 16);
-                tc_mma(dt, ad, bd, idesc, s > 0 ? 1u : 0u);
-            }
-            tc_commit(smem_u32(&s_mma[i & 1]));
-        };
-        if (tid == 0) issue(0);
-        for (int i = 0; i < nT; ++i) {
-            const int slot = resident ? i : i % RS;
-            if (tid == 0 && i + 1 < nT) issue(i + 1);
-            // the barrier parities of tile i's slot advance once per load
-            if (loaded_now || !resident) bphase ^= (1u << slot);
-            const bool ok = mbar_wait_bounded(smem_u32(&s_mma[i & 1]), (mphase >> (i & 1)) & 1u, p.spin_budget);
-            if (!ok) {
-                if (tid == 0) {
-                    record_error(p.status, 4 /* QT_ETIMEOUT */, 12);
-                    s_abort = 1;
-                }
-                mbar_wait_bounded(smem_u32(&s_mma[i & 1]), (mphase >> (i & 1)) & 1u, 1ll << 24);
-            }
-            mphase ^= (1u << (i & 1));
-            tc_fence_after();
-            // epilogue: this thread's row, its warpgroup's 128 columns, 8 chunks
-            const int lt = i < tA ? i : i - tA;
-#pragma unroll
-            for (int q = 0; q < kTcTileN / 64; q += 2) {
+            for (int q = 0; q < kTcTileN / 64; ++q) {
                 float va[32], vb[32];
-                tc_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
-                            (uint32_t)((i & 1) * kTcTileN + wg * (kTcTileN / 2) + q * 32),
-                        va);
-                tc_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) +
-                            (uint32_t)((i & 1) * kTcTileN + wg * (kTcTileN / 2) + (q + 1) * 32),
-                        vb);
+                tc_ld32(trow + (uint32_t)(q * 64), va);
+                tc_ld32(trow + (uint32_t)(q * 64 + 32), vb);
                 tc_wait_ld();
-                const float mcs[4] = {min16(va), min16(va + 16), min16(vb), min16(vb + 16)};
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const float mc = mcs[h];
-                    const int c = lt * (kTcTileN / kChunk) + wg * (kTcTileN / 2 / kChunk) + q * 2 + h;
-                    const bool t1 = mc < B1, t2 = mc < Bs;
-                    B3 = fminf(B3, fmaxf(mc, Bs));
-                    Bs = fminf(Bs, fmaxf(mc, B1));
-                    bcs = t1 ? bc : (t2 ? c : bcs);
-                    B1 = fminf(B1, mc);
-                    bc = t1 ? c : bc;
-                }
-            }
-            const bool endA = i == tA - 1, endB = i == nT - 1;
-            // the partner warpgroup hands its half-tile state to the owner of this grid
-            if ((endA && wg == 1) || (endB && wg == 0)) {
-                s_mB1[t] = B1;
-                s_mBs[t] = Bs;
-                s_mB3[t] = B3;
-                s_mbc[t] = bc;
-                s_mbcs[t] = bcs;
+                const int c0 = lt * (kTcTileN / kChunk) + q * 4;
+                tr.add(min16(va), c0);
+                tr.add(min16(va + 16), c0 + 1);
+                tr.add(min16(vb), c0 + 2);
+                tr.add(min16(vb + 16), c0 + 3);
             }
             tc_fence_before();
-            __syncthreads();      // accumulator i & 1, (streamed) slot of tile i and the hand-over are ready
-            if (tid == 0 && !resident && i + RS < nT) {
-                const uint32_t b = smem_u32(&s_bfull[slot]);
-                fence_proxy_async();
-                mbar_arrive_expect_tx(b, kTileBytes);
-                bulk_g2s(sB_u + slot * kTileBytes, tile_src(i + RS), kTileBytes, b);
+            mbar_arrive(smem_u32(&s_accempty[wg]));
+            return true;
+        };
+        auto dump = [&](int s, int gr) {
+            float* st = sst + ((s * 2 + gr) * 2 + wg) * 5 * kTcTileM + t;
+            st[0 * kTcTileM] = tr.B1;
+            st[1 * kTcTileM] = tr.Bs;
+            st[2 * kTcTileM] = tr.B3;
+            st[3 * kTcTileM] = __int_as_float(tr.bc);
+            st[4 * kTcTileM] = __int_as_float(tr.bcs);
+        };
+        for (long long n = 0;; ++n) {
+            const long long item = blockIdx.x + n * G;
+            if (item >= p.total_items) break;
+            if (__shfl_sync(0xFFFFFFFFu, *abort_flag, 0)) break;
+            if (item < lbeg || item >= lend) {
+                const LayerDesc& L = p.layers[layer_of(p, item)];
+                lbeg = L.item_begin;
+                lend = lbeg + L.items;
+                tA = p.grids[L.gridA].tc_tiles;
+                nT = tA + p.grids[L.gridB].tc_tiles;
             }
-            if ((endA && wg == 0) || (endB && wg == 1)) {
-                // merge the two half-tile states: the two smallest chunk minima
-                // (ties to the lower chunk), the rest into B3
-                float v4[4] = {B1, Bs, s_mB1[t], s_mBs[t]};
-                int c4[4] = {bc, bcs, s_mbc[t], s_mbcs[t]};
-                float rest = fminf(B3, s_mB3[t]);
-                int f = 0;
-#pragma unroll
-                for (int q = 1; q < 4; ++q)
-                    if (v4[q] < v4[f] || (v4[q] == v4[f] && c4[q] < c4[f])) f = q;
-                int g2 = f == 0 ? 1 : 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q != f && (v4[q] < v4[g2] || (v4[q] == v4[g2] && c4[q] < c4[g2]))) g2 = q;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q != f && q != g2) rest = fminf(rest, v4[q]);
-                const int mbc = c4[f], mbcs = c4[g2];
-                // re-score the two best chunks in FP32 and certify
-                const float inv_sg = ldexpf(1.0f, -Gown.tc_exp);
-                const float* recs = p.rec32 + Gown.roff * Rec32<DM>::kFloats;
-                const int nch = Gown.Npad / kChunk;      // chunks with FP32 records
-                int idx, idx2;
-                float best, S1, r1, best2, S12, r12;
-                cc_chunk<DM>(recs, mbc, xown, idx, best, S1, r1);
-                if (mbcs < nch && mbcs != mbc) {
-                    cc_chunk<DM>(recs, mbcs, xown, idx2, best2, S12, r12);
-                } else {
-                    idx2 = idx;
-                    best2 = S12 = __int_as_float(0x7F800000);
-                    r12 = r1;
+            const int s = (int)(n & 1);
+            bool ok = true;
+            // grid A: tiles i < tA with (g + i) & 1 == wg
+            tr.reset();
+            for (int i = (int)((g & 1) ^ wg); ok && i < tA; i += 2) ok = process(g + i, i);
+            if (ok) ok = warp_wait(smem_u32(&s_stempty[s]), (uint32_t)((n >> 1) & 1) ^ 1u, p.spin_budget);
+            if (ok) {
+                dump(s, 0);
+                mbar_arrive(smem_u32(&s_stA[s]));
+            }
+            // grid B
+            tr.reset();
+            for (int i = tA + (int)(((g + tA) & 1) ^ wg); ok && i < nT; i += 2) ok = process(g + i, i - tA);
+            if (ok) {
+                dump(s, 1);
+                mbar_arrive(smem_u32(&s_stB[s]));
+            }
+            if (!ok) {
+                if (lane == 0) {
+                    record_error(p.status, 4 /* QT_ETIMEOUT */, 26);
+                    *abort_flag = 1;
                 }
-                float in2;
+                break;
+            }
+            g += nT;
+        }
+    } else {
+        // ================================================================ certifiers
+        const int cw = warp - kCertWarp0;
+        const int t = cw * 32 + lane;
+        double* wpar = sparam + cw * PCpad;      // this warp's copy of the parameters of its draws' layer
+        float* wmu = s_mu[cw];                    // and the centres of that layer's two grids
+        SlotLayer* sl = s_slot[cw];               // [0], [1]: layer of the item in each slot; [2]: of the draws
+        long long dbeg = 0, dend = 0;             // items of the draws' layer
+        int slot_k[2] = {-1, -1};
+        auto fail = [&](int where) {
+            if (lane == 0) {
+                record_error(p.status, 4 /* QT_ETIMEOUT */, where);
+                *abort_flag = 1;
+            }
+        };
+        // Row t of item ordinal n into operand slot s: draw, centre, split.
+        auto draw = [&](long long n, int s) {
+            const long long item = blockIdx.x + n * G;
+            if (item < dbeg || item >= dend) {
+                const int k = layer_of(p, item);
+                const LayerDesc& L = p.layers[k];
+                const GridInfo& GA = p.grids[L.gridA];
+                const GridInfo& GB = p.grids[L.gridB];
+                __syncwarp();
+                if (p.source == kSampler) {
+                    const int pc = param_count(d);
+                    if (p.prec == 1) {
+                        float* f = reinterpret_cast<float*>(wpar);
+                        for (int e = lane; e < pc; e += 32) f[e] = p.params_f[(long long)k * p.params_stride + e];
+                    } else {
+                        for (int e = lane; e < pc; e += 32) wpar[e] = p.params_d[(long long)k * p.params_stride + e];
+                    }
+                }
+                if (lane < DM) {
+                    wmu[lane] = GA.mu[lane];
+                    wmu[DM + lane] = GB.mu[lane];
+                }
+                if (lane == 0) {
+                    SlotLayer& D = sl[2];
+                    D.item_begin = L.item_begin;
+                    D.coff = L.coff;
+                    D.goffA = GA.goff;
+                    D.goffB = GB.goff;
+                    D.roffA = GA.roff;
+                    D.roffB = GB.roff;
+                    D.k = k;
+                    D.NA = L.NA;
+                    D.NB = L.NB;
+                    D.NpadA = GA.Npad;
+                    D.NpadB = GB.Npad;
+                    D.expA = GA.tc_exp;
+                    D.expB = GB.tc_exp;
+                }
+                __syncwarp();
+                dbeg = L.item_begin;
+                dend = dbeg + L.items;
+            }
+            const SlotLayer& D = sl[2];
+            if (slot_k[s] != D.k) {
+                if (lane == 0) sl[s] = D;
+                __syncwarp();
+                slot_k[s] = D.k;
+            }
+            const unsigned long long mtile = (unsigned long long)(item - D.item_begin) * kTcTileM;
+            const unsigned long long ms = mtile + (unsigned long long)t;
+            const Centred<DM> cs = centred_sample_inl<DM>(p, reinterpret_cast<const float*>(wpar), wpar, wmu,
+                                                          wmu + DM, D.k, ms < p.M ? ms : mtile);
+#pragma unroll
+            for (int gr = 0; gr < 2; ++gr) {
+                const float* x = gr == 0 ? cs.xa : cs.yb;
+                const float A = gr == 0 ? cs.Aa : cs.Ab;
+                const float sg = ldexpf(1.0f, gr == 0 ? D.expA : D.expB);
+                bool big = false;
+#pragma unroll
+                for (int l = 0; l < DM; ++l)
+                    if (l < d) big = big || !(fabsf(sg * x[l]) <= 16384.0f);
+                uint32_t hi[DM], lo[DM];
+#pragma unroll
+                for (int l = 0; l < DM; ++l) {
+                    const float v = (l < d && !big) ? sg * x[l] : 0.0f;
+                    const __half h = __float2half_rn(v);
+                    hi[l] = __half_as_ushort(h);
+                    lo[l] = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+                }
+                const uint32_t one = __half_as_ushort(__float2half_rn(1.0f));
+                uint32_t w[K / 2];
+#pragma unroll
+                for (int q = 0; q < K; q += 2) {
+                    uint32_t h2[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int c = q + u;
+                        h2[u] = c < DM ? hi[c] : (c < 2 * DM ? hi[c - DM] : (c < 3 * DM ? lo[c - 2 * DM] : (c < 3 * DM + 2 ? one : 0u)));
+                    }
+                    w[q / 2] = h2[0] | (h2[1] << 16);
+                }
+                unsigned char* base = ops + (s * 2 + gr) * kOpBytes;
+#pragma unroll
+                for (int kb = 0; kb < K / 8; ++kb)
+                    *reinterpret_cast<uint4*>(base + (((t >> 3) * (K / 8) + kb) * 64 + (t & 7) * 8) * 2) =
+                        make_uint4(w[4 * kb], w[4 * kb + 1], w[4 * kb + 2], w[4 * kb + 3]);
+                float* cx = scert + (s * 2 + gr) * (DM + 1) * kTcTileM + t;
+#pragma unroll
+                for (int l = 0; l < DM; ++l) cx[l * kTcTileM] = x[l];
+                cx[DM * kTcTileM] = __int_as_float(__float_as_int(A) | (big ? (int)0x80000000 : 0));
+            }
+        };
+        // Merge the warpgroups' chunk states of row t, re-score the best chunk
+        // in FP32 (and the second one when the certificate needs it) and
+        // certify; returns the cell, sets `need`.
+        auto certify = [&](int s, int gr, const SlotLayer& S, bool valid, bool& need) -> int {
+            const int Npad = gr == 0 ? S.NpadA : S.NpadB;
+            const int Nown = gr == 0 ? S.NA : S.NB;
+            const float* st = sst + (s * 2 + gr) * 2 * 5 * kTcTileM + t;
+            float v0 = st[0], v1 = st[kTcTileM], v2 = st[5 * kTcTileM], v3 = st[6 * kTcTileM];
+            int c0 = __float_as_int(st[3 * kTcTileM]), c1 = __float_as_int(st[4 * kTcTileM]);
+            int c2 = __float_as_int(st[8 * kTcTileM]), c3 = __float_as_int(st[9 * kTcTileM]);
+            float rest = fminf(st[2 * kTcTileM], st[7 * kTcTileM]);
+            pair_sort2(v0, c0, v1, c1);
+            pair_sort2(v2, c2, v3, c3);
+            pair_sort2(v0, c0, v2, c2);
+            pair_sort2(v1, c1, v3, c3);
+            pair_sort2(v1, c1, v2, c2);
+            rest = fminf(rest, fminf(v2, v3));
+            const int nch = Npad / kChunk;
+            const float* cx = scert + (s * 2 + gr) * (DM + 1) * kTcTileM + t;
+            float x[DM];
+#pragma unroll
+            for (int l = 0; l < DM; ++l) x[l] = cx[l * kTcTileM];
+            const float Araw = cx[DM * kTcTileM];
+            const bool big = (__float_as_int(Araw) & (int)0x80000000) != 0;
+            const float A = fabsf(Araw);
+            const float inv_sg = ldexpf(1.0f, -(gr == 0 ? S.expA : S.expB));
+            const float* recs = p.rec32 + (gr == 0 ? S.roffA : S.roffB) * F;
+            const bool chunk_ok = c0 >= 0 && c0 < nch;
+            const int mbc = chunk_ok ? c0 : 0;
+            int idx;
+            float best, in2, r1;
+            cc_chunk<DM>(recs, mbc, x, idx, best, in2, r1);
+            // first: FP32 inside the best chunk, tensor-core scores outside it
+            int why = 0;
+            bool tcok = tc_certified(d, A, best, in2, fminf(v1, rest) * inv_sg * inv_sg, r1, inv_sg, why);
+            if (!tcok && why == 2 && c1 >= 0 && c1 < nch && c1 != mbc) {
+                // the second chunk competes: FP32 inside both, tensor-core scores outside
+                int idx2;
+                float best2, S12, r12;
+                cc_chunk<DM>(recs, c1, x, idx2, best2, S12, r12);
                 if (best2 < best || (best2 == best && idx2 < idx)) {
                     in2 = fminf(S12, best);
                     best = best2;
                     idx = idx2;
                     r1 = r12;
                 } else {
-                    in2 = fminf(S1, best2);
+                    in2 = fminf(in2, best2);
                 }
-                const float B3cc = rest * inv_sg * inv_sg;
-                int why = 0;
-                const bool tcok = tc_certified(d, Aown, best, in2, B3cc, r1, inv_sg, why);
-                const bool rng_ok = idx < Gown.N && !big;
-                const bool cert = tcok && rng_ok;
-                if (valid && !cert) atomicAdd(&p.status->spare[!rng_ok ? 3 : why], 1ull);
-                cown = idx;
-                need = !cert && valid;
+                tcok = tc_certified(d, A, best, in2, rest * inv_sg * inv_sg, r1, inv_sg, why);
             }
-            if (endA || endB) {
-                B1 = Bs = B3 = __int_as_float(0x7F800000);
-                bc = 0;
-                bcs = 1;
-            }
-            if (s_abort) {
-                // the MMA of tile i + 1 may be in flight: let it finish before leaving
-                if (i + 1 < nT) {
-                    mbar_wait_bounded(smem_u32(&s_mma[(i + 1) & 1]), (mphase >> ((i + 1) & 1)) & 1u, 1ll << 24);
-                    mphase ^= (1u << ((i + 1) & 1));
-                }
-                break;
-            }
-        }
-        if (resident) loaded_now = false;
-        if (s_abort) break;
-
-        // ---- uncertified searches of this warpgroup's grid: exact window search
-        {
+            const bool rng_ok = chunk_ok && idx < Nown && !big;
+            const bool cert = tcok && rng_ok;
+            if (valid && !cert) atomicAdd(&p.status->spare[!rng_ok ? 3 : why], 1ull);
+            need = valid && !cert;
+            return idx;
+        };
+        // exact window search of the lanes in `need` (the whole warp takes part)
+        auto recheck = [&](int s, int gr, const SlotLayer& S, unsigned long long ms, bool need, int& cell) {
             unsigned mask = __ballot_sync(0xFFFFFFFFu, need);
+            if (!mask) return;
+            const float* cx = scert + (s * 2 + gr) * (DM + 1) * kTcTileM + t;
+            float xs[DM];
+#pragma unroll
+            for (int l = 0; l < DM; ++l) xs[l] = cx[l * kTcTileM];
+            const float A = fabsf(cx[DM * kTcTileM]);
+            const int k = S.k;
+            const float* gpf = p.params_f ? p.params_f + (long long)k * p.params_stride : nullptr;
+            const double* gpd = p.params_d ? p.params_d + (long long)k * p.params_stride : nullptr;
+            const float* recs = p.rec32 + (gr == 0 ? S.roffA : S.roffB) * F;
+            const double* g64 = p.g64 + (gr == 0 ? S.goffA : S.goffB) * d;
+            const int Npad = gr == 0 ? S.NpadA : S.NpadB;
+            const int Nown = gr == 0 ? S.NA : S.NB;
             while (mask) {
                 const int src = __ffs(mask) - 1;
                 mask &= mask - 1;
                 double z[DM];
-                if (lane == src) exact_sample<DM>(p, s_pf, s_pd, k, ms, wg == 1, z);
-                const int r = warp_window_nn<DM>(xown, Aown, z, src, p.rec32 + Gown.roff * Rec32<DM>::kFloats,
-                                                 Gown.Npad, p.g64 + Gown.goff * d, Gown.N, d);
-                if (lane == src) cown = r;
+                if (lane == src) exact_sample<DM>(p, gpf, gpd, k, ms, gr == 1, z);
+                const int r = warp_window_nn<DM>(xs, A, z, src, recs, Npad, g64, Nown, d);
+                if (lane == src) cell = r;
                 if (lane == 0) atomicAdd(&p.status->rechecks, 1ull);
             }
+        };
+        if (blockIdx.x < p.total_items) {
+            draw(0, 0);
+            fence_proxy_async();
+            mbar_arrive(smem_u32(&s_opfull[0]));
         }
-        if (wg == 1) s_mbc[t] = cown;     // hand cell j to warpgroup 0
-        __syncthreads();
-
-        // ---- counters p^k_ij
-        if (wg == 0 && valid) {
-            const int ci = cown, cj = s_mbc[t];
-            if ((unsigned)ci >= (unsigned)L.NA || (unsigned)cj >= (unsigned)L.NB) {
-                record_error(p.status, 6 /* QT_EDEVICE */, 13);
-            } else {
-                count_add(p.counts, p.counts_u32, L.coff + (long long)ci * L.NB + cj, 1u);
-                if (p.cellsA) {
-                    p.cellsA[ms] = ci;
-                    p.cellsB[ms] = cj;
+        for (long long n = 0;; ++n) {
+            const long long item = blockIdx.x + n * G;
+            if (item >= p.total_items) break;
+            if (__shfl_sync(0xFFFFFFFFu, *abort_flag, 0)) break;
+            // operands of the next item: its slot is free once item n - 1's MMAs are done
+            if (item + G < p.total_items) {
+                const int s1 = (int)((n + 1) & 1);
+                if (!warp_wait(smem_u32(&s_opempty[s1]), (uint32_t)(((n + 1) >> 1) & 1) ^ 1u, p.spin_budget)) {
+                    fail(27);
+                    break;
                 }
-                if (p.dump_count > 0 && (ms % (unsigned long long)p.dump_stride) == 0ull) {
-                    const unsigned long long tt = ms / (unsigned long long)p.dump_stride;
-                    if (tt < (unsigned long long)p.dump_count) {
-                        const long long row = (long long)k * p.dump_count + (long long)tt;
-                        double zx[DM], zy[DM];
-                        exact_sample<DM>(p, s_pf, s_pd, k, ms, false, zx);
-                        exact_sample<DM>(p, s_pf, s_pd, k, ms, true, zy);
-                        for (int l = 0; l < d; ++l) {
-                            p.dumpX[row * d + l] = zx[l];
-                            p.dumpY[row * d + l] = zy[l];
+                draw(n + 1, s1);
+                fence_proxy_async();
+                mbar_arrive(smem_u32(&s_opfull[s1]));
+            }
+            const int s = (int)(n & 1);
+            const SlotLayer& S = sl[s];
+            const unsigned long long ms = (unsigned long long)(item - S.item_begin) * kTcTileM + (unsigned long long)t;
+            const bool valid = ms < p.M;
+            bool needA = false, needB = false;
+            if (!warp_wait(smem_u32(&s_stA[s]), (uint32_t)((n >> 1) & 1), p.spin_budget)) {
+                fail(28);
+                break;
+            }
+            int ci = certify(s, 0, S, valid, needA);
+            if (!warp_wait(smem_u32(&s_stB[s]), (uint32_t)((n >> 1) & 1), p.spin_budget)) {
+                fail(29);
+                break;
+            }
+            int cj = certify(s, 1, S, valid, needB);
+            mbar_arrive(smem_u32(&s_stempty[s]));
+            recheck(s, 0, S, ms, needA, ci);
+            recheck(s, 1, S, ms, needB, cj);
+            // ---- counters p^k_ij
+            if (valid) {
+                if ((unsigned)ci >= (unsigned)S.NA || (unsigned)cj >= (unsigned)S.NB) {
+                    record_error(p.status, 6 /* QT_EDEVICE */, 13);
+                } else {
+                    count_add(p.counts, p.counts_u32, S.coff + (long long)ci * S.NB + cj, 1u);
+                    if (p.cellsA) {
+                        p.cellsA[ms] = ci;
+                        p.cellsB[ms] = cj;
+                    }
+                    if (p.dump_count > 0 && (ms % (unsigned long long)p.dump_stride) == 0ull) {
+                        const unsigned long long tt = ms / (unsigned long long)p.dump_stride;
+                        if (tt < (unsigned long long)p.dump_count) {
+                            const int k = S.k;
+                            const long long row = (long long)k * p.dump_count + (long long)tt;
+                            const float* gpf = p.params_f ? p.params_f + (long long)k * p.params_stride : nullptr;
+                            const double* gpd = p.params_d ? p.params_d + (long long)k * p.params_stride : nullptr;
+                            double zx[DM], zy[DM];
+                            exact_sample<DM>(p, gpf, gpd, k, ms, false, zx);
+                            exact_sample<DM>(p, gpf, gpd, k, ms, true, zy);
+                            for (int l = 0; l < d; ++l) {
+                                p.dumpX[row * d + l] = zx[l];
+                                p.dumpY[row * d + l] = zy[l];
+                            }
+                            p.dumpI[row] = ci;
+                            p.dumpJ[row] = cj;
                         }
-                        p.dumpI[row] = ci;
-                        p.dumpJ[row] = cj;
                     }
                 }
             }
         }
-        __syncthreads();
     }
 
-    // ---- release the tensor memory (every MMA issued has completed: each was waited)
+    // ---- every role is done; the producer has drained the MMAs and copies
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -579,13 +885,15 @@ static cudaError_t launch_tc(const ForwardParams& p, int dyn, int num_sms, int* 
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
     int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 256, dyn);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kTcThreads, dyn);
     if (e != cudaSuccess) return e;
     if (b != 1) return cudaErrorInvalidConfiguration;   // one CTA per SM: it owns all 512 TMEM columns
+    if (p.tc_slots < 2 || p.tc_slots > kTcMaxSlots) return cudaErrorInvalidValue;
     *bps = b;
     long long grid = (long long)num_sms * b;
     if (grid > p.total_items) grid = p.total_items;
-    kern<<<(unsigned)grid, 256, dyn, st>>>(p);
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, kTcThreads, dyn, st>>>(p);
     return cudaGetLastError();
 }
 

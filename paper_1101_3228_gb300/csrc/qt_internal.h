@@ -49,6 +49,18 @@ struct GridInfo {
 
 constexpr int kTcTileN = 256;      // grid points per tensor-core operand tile (MMA N)
 constexpr int kTcTileM = 128;      // samples per tensor-core work item (MMA M)
+constexpr int kTcThreads = 416;    // tensor-core form: 13 warps (8 epilogue, 1 producer, 4 certifier)
+constexpr int kTcMaxSlots = 16;    // tensor-core form: most operand tiles held in shared memory
+
+// Dynamic shared memory of the tensor-core form besides its ring of operand
+// tiles (dimension class dm, K columns per operand row).
+__host__ __device__ constexpr long long tc_fixed_smem(int dm, int K)
+{
+    return 4ll * kTcTileM * K * 2                            // sample operands: 2 items x 2 grids
+           + 2ll * 2 * 2 * 5 * kTcTileM * 4                  // chunk states: 2 items x 2 grids x 2 warpgroups x 5
+           + 2ll * 2 * (dm + 1) * kTcTileM * 4               // centred samples: 2 items x 2 grids x (dm + 1)
+           + 4ll * ((2 * dm + 3 * dm * dm + 1) / 2 * 2) * 8; // layer parameters, one copy per certifier warp
+}
 
 struct ForwardParams {
     // problem
