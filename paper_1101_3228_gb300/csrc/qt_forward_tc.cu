@@ -304,9 +304,11 @@ __global__ void prep_tc_tiles_kernel(const float* __restrict__ rec32, GridInfo* 
 namespace {
 
 constexpr int kEpiWarps = 8;       // warps 0-7: epilogue warpgroups 0 and 1
-constexpr int kProducerWarp = 8;   // warp 8: operand tiles and MMAs
-constexpr int kCertWarp0 = 9;      // warps 9-12: draw, certify, recheck, count
-static_assert(kTcThreads == 13 * 32, "role layout");
+constexpr int kMmaWarp0 = 8;       // warps 8, 9: MMAs for epilogue warpgroups 0, 1
+constexpr int kLoadWarp = 10;      // warp 10: bulk copies of the operand tiles
+constexpr int kCertWarp0 = 11;     // warps 11-14: draw, certify, recheck, count
+constexpr int kHalfN = kTcTileN / 2;   // columns of one accumulator (MMA N)
+static_assert(kTcThreads == 15 * 32, "role layout");
 
 // What a certifier warp needs of the layer of an item (shared memory, one per
 // warp and operand slot, plus one for the layer of its draws).
@@ -330,10 +332,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
     const float kInf = __int_as_float(0x7F800000);
     extern __shared__ __align__(128) unsigned char dsm_tc[];
     __shared__ __align__(8) unsigned long long s_tfull[kTcMaxSlots], s_tempty[kTcMaxSlots];
-    __shared__ __align__(8) unsigned long long s_accfull[2], s_accempty[2];
+    __shared__ __align__(8) unsigned long long s_accfull[4], s_accempty[4];
     __shared__ __align__(8) unsigned long long s_opfull[2], s_opempty[2];
     __shared__ __align__(8) unsigned long long s_stA[2], s_stB[2], s_stempty[2];
-    __shared__ __align__(8) unsigned long long s_drain;
+    __shared__ __align__(8) unsigned long long s_drain[2], s_ldone;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ SlotLayer s_slot[4][3];
@@ -358,16 +360,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
             mbar_init(smem_u32(&s_tfull[i]), 1);
             mbar_init(smem_u32(&s_tempty[i]), 1);
         }
+        for (int a = 0; a < 4; ++a) {
+            mbar_init(smem_u32(&s_accfull[a]), 1);
+            mbar_init(smem_u32(&s_accempty[a]), 128);
+        }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&s_accfull[b]), 1);
-            mbar_init(smem_u32(&s_accempty[b]), 128);
             mbar_init(smem_u32(&s_opfull[b]), 128);
-            mbar_init(smem_u32(&s_opempty[b]), 1);
+            mbar_init(smem_u32(&s_opempty[b]), 2);
             mbar_init(smem_u32(&s_stA[b]), 256);
             mbar_init(smem_u32(&s_stB[b]), 256);
             mbar_init(smem_u32(&s_stempty[b]), 128);
         }
-        mbar_init(smem_u32(&s_drain), 1);
+        mbar_init(smem_u32(&s_drain[0]), 1);
+        mbar_init(smem_u32(&s_drain[1]), 1);
+        mbar_init(smem_u32(&s_ldone), 2);
         s_abort = 0;
         fence_proxy_async();
     }
@@ -383,139 +389,102 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
     const uint32_t tmem = s_tmem;
     volatile int* abort_flag = &s_abort;
 
-    if (warp == kProducerWarp) {
-        // ================================================================ producer
+    if (warp == kMmaWarp0 || warp == kMmaWarp0 + 1) {
+        // ================================================================ MMAs
+        // tile g of the CTA's sequence goes to warpgroup g & 1, which has its
+        // own issuing warp; the tile's two 128-point halves go to that
+        // warpgroup's accumulators 2 (g & 1) + h
+        const int ib = warp - kMmaWarp0;
         if (lane == 0) {
             const bool resident = p.tc_resident != 0;
-            const unsigned char* tiles = reinterpret_cast<const unsigned char*>(p.tc_tiles);
-            const uint32_t idesc =
-                (1u << 4) | ((uint32_t)(kTcTileN >> 3) << 17) | ((uint32_t)(kTcTileM >> 4) << 24);
-            int cur = -1, tA = 0, nT = 0;
-            long long toffA = 0, toffB = 0, lbeg = 0, lend = 0;
-            uint32_t tph = 0, pend = 0, drains = 0;
-            long long qc = 0, ql = 0;          // streamed ring: positions consumed, loaded
-            long long ln = 0;                  // streamed ring: load cursor (item ordinal, tile)
-            int li = 0, ltA = 0, lnT = 0;
-            long long ltoffA = 0, ltoffB = 0, llbeg = 0, llend = 0;
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(kHalfN >> 3) << 17) | ((uint32_t)(kTcTileM >> 4) << 24);
+            int tA = 0, nT = 0, layers = 0, lastT = 0;
+            long long lbeg = 0, lend = 0;
+            uint32_t tph = 0, pend = 0;        // resident: parity of each slot's current load, slots not yet waited
+            int rslot = ib;                    // streamed: ring slot and parity of this warp's next tile
+            uint32_t rph = 0;
+            if (!resident && rslot >= RS) {
+                rslot -= RS;
+                rph = 1;
+            }
+            long long g = 0;                   // tiles of the CTA's sequence so far
+            bool ok = true;
             auto fail = [&](int where) {
                 record_error(p.status, 4 /* QT_ETIMEOUT */, where);
                 *abort_flag = 1;
+                ok = false;
             };
-            // streamed ring: issue the copies of the positions before `upto`
-            auto load_ahead = [&](long long upto) -> bool {
-                while (ql < upto) {
-                    const long long item = blockIdx.x + ln * G;
-                    if (item >= p.total_items) return true;
-                    if (li == 0 && (item < llbeg || item >= llend)) {
-                        const LayerDesc& L = p.layers[layer_of(p, item)];
-                        llbeg = L.item_begin;
-                        llend = llbeg + L.items;
-                        ltA = p.grids[L.gridA].tc_tiles;
-                        lnT = ltA + p.grids[L.gridB].tc_tiles;
-                        ltoffA = p.grids[L.gridA].tc_toff;
-                        ltoffB = p.grids[L.gridB].tc_toff;
-                    }
-                    const int r = (int)(ql % RS);
-                    if (!mbar_wait_bounded(smem_u32(&s_tempty[r]), (uint32_t)((ql / RS) & 1) ^ 1u, p.spin_budget))
-                        return false;
-                    const long long src = li < ltA ? ltoffA + li : ltoffB + (li - ltA);
-                    mbar_arrive_expect_tx(smem_u32(&s_tfull[r]), kTileBytes);
-                    bulk_g2s(ring_u + r * kTileBytes, tiles + src * kTileBytes, kTileBytes, smem_u32(&s_tfull[r]));
-                    ++ql;
-                    if (++li == lnT) {
-                        li = 0;
-                        ++ln;
-                    }
-                }
-                return true;
-            };
-            bool ok = resident || load_ahead(RS - 1);
-            if (!ok) fail(20);
-            long long g = 0;                   // tiles issued so far: tile g goes to accumulator g & 1
             for (long long n = 0; ok; ++n) {
                 const long long item = blockIdx.x + n * G;
                 if (item >= p.total_items || *abort_flag) break;
                 if (item < lbeg || item >= lend) {
-                    const int k = layer_of(p, item);
-                    const LayerDesc& L = p.layers[k];
+                    const LayerDesc& L = p.layers[layer_of(p, item)];
                     lbeg = L.item_begin;
                     lend = lbeg + L.items;
                     tA = p.grids[L.gridA].tc_tiles;
                     nT = tA + p.grids[L.gridB].tc_tiles;
-                    toffA = p.grids[L.gridA].tc_toff;
-                    toffB = p.grids[L.gridB].tc_toff;
                     if (resident) {
-                        if (cur >= 0) {
-                            // the previous layer's MMAs read the slots about to be overwritten
-                            tc_commit(smem_u32(&s_drain));
-                            if (!mbar_wait_bounded(smem_u32(&s_drain), drains & 1u, p.spin_budget)) {
-                                fail(21);
-                                break;
-                            }
-                            ++drains;
+                        // the loader overwrites the tiles once both warps' MMAs of the previous layer are done
+                        if (layers > 0) {
+                            tc_commit(smem_u32(&s_ldone));
+                            for (int i = 0; i < lastT; ++i) tph ^= 1u << i;
                         }
-                        for (int i = 0; i < nT; ++i) {
-                            const long long src = i < tA ? toffA + i : toffB + (i - tA);
-                            mbar_arrive_expect_tx(smem_u32(&s_tfull[i]), kTileBytes);
-                            bulk_g2s(ring_u + i * kTileBytes, tiles + src * kTileBytes, kTileBytes,
-                                     smem_u32(&s_tfull[i]));
-                            pend |= 1u << i;
-                        }
+                        pend = nT >= 32 ? ~0u : ((1u << nT) - 1u);
+                        lastT = nT;
                     }
-                    cur = k;
+                    ++layers;
                 }
                 const int os = (int)(n & 1);
                 if (!mbar_wait_bounded(smem_u32(&s_opfull[os]), (uint32_t)((n >> 1) & 1), p.spin_budget)) {
                     fail(22);
                     break;
                 }
-                for (int i = 0; i < nT; ++i) {
+                for (int i = (int)((g & 1) ^ (long long)ib); i < nT && ok; i += 2) {
                     const long long gg = g + i;
-                    const int b = (int)(gg & 1);
-                    if (!mbar_wait_bounded(smem_u32(&s_accempty[b]), (uint32_t)((gg >> 1) & 1) ^ 1u,
-                                           p.spin_budget)) {
-                        fail(23);
-                        ok = false;
-                        break;
-                    }
                     int slot;
                     if (resident) {
                         slot = i;
                         if ((pend >> i) & 1u) {
                             if (!mbar_wait_bounded(smem_u32(&s_tfull[i]), (tph >> i) & 1u, p.spin_budget)) {
                                 fail(24);
-                                ok = false;
                                 break;
                             }
-                            tph ^= 1u << i;
                             pend &= ~(1u << i);
                         }
                     } else {
-                        slot = (int)(qc % RS);
-                        if (!mbar_wait_bounded(smem_u32(&s_tfull[slot]), (uint32_t)((qc / RS) & 1), p.spin_budget)) {
+                        slot = rslot;
+                        if (!mbar_wait_bounded(smem_u32(&s_tfull[slot]), rph, p.spin_budget)) {
                             fail(24);
-                            ok = false;
                             break;
                         }
                     }
-                    tc_fence_after();
                     const uint32_t a_base = ops_u + (uint32_t)((os * 2 + (i < tA ? 0 : 1)) * kOpBytes);
-                    const uint32_t b_base = ring_u + (uint32_t)(slot * kTileBytes);
-                    const uint32_t dt = tmem + (uint32_t)(b * kTcTileN);
 #pragma unroll
-                    for (int s = 0; s < KT; ++s) {
-                        const uint64_t ad = smem_desc(a_base + s * 256, 128, K * 16);
-                        const uint64_t bd = smem_desc(b_base + s * 256, 128, K * 16);
-                        tc_mma(dt, ad, bd, idesc, s > 0 ? 1u : 0u);
-                    }
-                    tc_commit(smem_u32(&s_accfull[b]));
-                    if (!resident) {
-                        tc_commit(smem_u32(&s_tempty[slot]));
-                        ++qc;
-                        if (!load_ahead(qc + RS - 1)) {
-                            fail(25);
-                            ok = false;
+                    for (int h = 0; h < 2; ++h) {
+                        const int acc = 2 * ib + h;
+                        if (!mbar_wait_bounded(smem_u32(&s_accempty[acc]), (uint32_t)((gg >> 1) & 1) ^ 1u,
+                                               p.spin_budget)) {
+                            fail(23);
                             break;
+                        }
+                        tc_fence_after();
+                        // rows 128h .. 128h + 127 of the tile: 16 row blocks of K * 16 bytes further
+                        const uint32_t b_base = ring_u + (uint32_t)(slot * kTileBytes + h * (kHalfN / 8) * K * 16);
+                        const uint32_t dt = tmem + (uint32_t)(acc * kHalfN);
+#pragma unroll
+                        for (int s = 0; s < KT; ++s) {
+                            const uint64_t ad = smem_desc(a_base + s * 256, 128, K * 16);
+                            const uint64_t bd = smem_desc(b_base + s * 256, 128, K * 16);
+                            tc_mma(dt, ad, bd, idesc, s > 0 ? 1u : 0u);
+                        }
+                        tc_commit(smem_u32(&s_accfull[acc]));
+                    }
+                    if (ok && !resident) {
+                        tc_commit(smem_u32(&s_tempty[slot]));
+                        rslot += 2;
+                        if (rslot >= RS) {
+                            rslot -= RS;
+                            rph ^= 1u;
                         }
                     }
                 }
@@ -523,43 +492,120 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                 tc_commit(smem_u32(&s_opempty[os]));
                 g += nT;
             }
-            // every MMA issued completes and every copy issued lands before the
-            // tensor memory and the shared memory are released
-            tc_commit(smem_u32(&s_drain));
-            mbar_wait_bounded(smem_u32(&s_drain), drains & 1u, 1ll << 24);
+            // every MMA issued completes before the tensor memory is released
+            tc_commit(smem_u32(&s_drain[ib]));
+            mbar_wait_bounded(smem_u32(&s_drain[ib]), 0u, 1ll << 24);
+        }
+    } else if (warp == kLoadWarp) {
+        // ================================================================ operand tiles
+        if (lane == 0) {
+            const bool resident = p.tc_resident != 0;
+            const unsigned char* tiles = reinterpret_cast<const unsigned char*>(p.tc_tiles);
+            long long lbeg = 0, lend = 0, toffA = 0, toffB = 0;
+            int tA = 0, nT = 0;
+            auto refresh = [&](long long item) {
+                const LayerDesc& L = p.layers[layer_of(p, item)];
+                lbeg = L.item_begin;
+                lend = lbeg + L.items;
+                tA = p.grids[L.gridA].tc_tiles;
+                nT = tA + p.grids[L.gridB].tc_tiles;
+                toffA = p.grids[L.gridA].tc_toff;
+                toffB = p.grids[L.gridB].tc_toff;
+            };
+            auto copy = [&](int slot, int i) {
+                const long long src = i < tA ? toffA + i : toffB + (i - tA);
+                mbar_arrive_expect_tx(smem_u32(&s_tfull[slot]), kTileBytes);
+                bulk_g2s(ring_u + slot * kTileBytes, tiles + src * kTileBytes, kTileBytes, smem_u32(&s_tfull[slot]));
+            };
+            auto fail = [&](int where) {
+                record_error(p.status, 4 /* QT_ETIMEOUT */, where);
+                *abort_flag = 1;
+            };
             if (resident) {
-                for (int i = 0; i < kTcMaxSlots; ++i)
-                    if ((pend >> i) & 1u) mbar_wait_bounded(smem_u32(&s_tfull[i]), (tph >> i) & 1u, 1ll << 24);
+                // all tiles of a layer pair, once per layer
+                int layers = 0, lastT = 0;
+                uint32_t tph = 0;              // per slot: parity of the next load's completion
+                for (long long n = 0;; ++n) {
+                    const long long item = blockIdx.x + n * G;
+                    if (item >= p.total_items || *abort_flag) break;
+                    if (item >= lbeg && item < lend) continue;
+                    refresh(item);
+                    if (layers > 0 &&
+                        !mbar_wait_bounded(smem_u32(&s_ldone), (uint32_t)((layers - 1) & 1), p.spin_budget)) {
+                        fail(21);
+                        break;
+                    }
+                    if (layers > 0)
+                        for (int i = 0; i < lastT; ++i) tph ^= 1u << i;
+                    for (int i = 0; i < nT; ++i) copy(i, i);
+                    lastT = nT;
+                    ++layers;
+                }
+                // the last layer's copies land before the shared memory is released
+                for (int i = 0; i < lastT; ++i) mbar_wait_bounded(smem_u32(&s_tfull[i]), (tph >> i) & 1u, 1ll << 24);
             } else {
-                for (long long q = qc; q < ql; ++q)
-                    mbar_wait_bounded(smem_u32(&s_tfull[q % RS]), (uint32_t)((q / RS) & 1), 1ll << 24);
+                // the tiles of every item in order, through the ring
+                long long ql = 0, ln = 0;
+                int li = 0, r = 0;
+                uint32_t rph = 0;              // parity of the ring's current lap
+                while (true) {
+                    const long long item = blockIdx.x + ln * G;
+                    if (item >= p.total_items || *abort_flag) break;
+                    if (li == 0 && (item < lbeg || item >= lend)) refresh(item);
+                    if (!mbar_wait_bounded(smem_u32(&s_tempty[r]), rph ^ 1u, p.spin_budget)) {
+                        fail(25);
+                        break;
+                    }
+                    copy(r, li);
+                    ++ql;
+                    if (++r == RS) {
+                        r = 0;
+                        rph ^= 1u;
+                    }
+                    if (++li == nT) {
+                        li = 0;
+                        ++ln;
+                    }
+                }
+                // the copies of the last lap land before the shared memory is released
+                for (int q = 0; q < RS && q < ql; ++q) {
+                    if (--r < 0) {
+                        r = RS - 1;
+                        rph ^= 1u;
+                    }
+                    mbar_wait_bounded(smem_u32(&s_tfull[r]), rph, 1ll << 24);
+                }
             }
         }
     } else if (warp < kEpiWarps) {
         // ================================================================ epilogue
         const int wg = warp >> 2;
         const int t = (warp & 3) * 32 + lane;
-        const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(wg * kTcTileN);
+        const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         int tA = 0, nT = 0;
         long long g = 0, lbeg = 0, lend = 0;
         ChunkTrack tr;
         auto process = [&](long long gg, int lt) -> bool {
-            if (!warp_wait(smem_u32(&s_accfull[wg]), (uint32_t)((gg >> 1) & 1), p.spin_budget)) return false;
-            tc_fence_after();
 #pragma unroll
-            for (int q = 0; q < kTcTileN / 64; ++q) {
-                float va[32], vb[32];
-                tc_ld32(trow + (uint32_t)(q * 64), va);
-                tc_ld32(trow + (uint32_t)(q * 64 + 32), vb);
-                tc_wait_ld();
-                const int c0 = lt * (kTcTileN / kChunk) + q * 4;
-                tr.add(min16(va), c0);
-                tr.add(min16(va + 16), c0 + 1);
-                tr.add(min16(vb), c0 + 2);
-                tr.add(min16(vb + 16), c0 + 3);
+            for (int h = 0; h < 2; ++h) {
+                const int acc = 2 * wg + h;
+                if (!warp_wait(smem_u32(&s_accfull[acc]), (uint32_t)((gg >> 1) & 1), p.spin_budget)) return false;
+                tc_fence_after();
+#pragma unroll
+                for (int q = 0; q < kHalfN / 64; ++q) {
+                    float va[32], vb[32];
+                    tc_ld32(trow + (uint32_t)(acc * kHalfN + q * 64), va);
+                    tc_ld32(trow + (uint32_t)(acc * kHalfN + q * 64 + 32), vb);
+                    tc_wait_ld();
+                    const int c0 = lt * (kTcTileN / kChunk) + h * (kHalfN / kChunk) + q * 4;
+                    tr.add(min16(va), c0);
+                    tr.add(min16(va + 16), c0 + 1);
+                    tr.add(min16(vb), c0 + 2);
+                    tr.add(min16(vb + 16), c0 + 3);
+                }
+                tc_fence_before();
+                mbar_arrive(smem_u32(&s_accempty[acc]));
             }
-            tc_fence_before();
-            mbar_arrive(smem_u32(&s_accempty[wg]));
             return true;
         };
         auto dump = [&](int s, int gr) {

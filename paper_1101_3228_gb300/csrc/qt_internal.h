@@ -49,7 +49,7 @@ struct GridInfo {
 
 constexpr int kTcTileN = 256;      // grid points per tensor-core operand tile (MMA N)
 constexpr int kTcTileM = 128;      // samples per tensor-core work item (MMA M)
-constexpr int kTcThreads = 416;    // tensor-core form: 13 warps (8 epilogue, 1 producer, 4 certifier)
+constexpr int kTcThreads = 480;    // tensor-core form: 15 warps (8 epilogue, 2 MMA, loader, 4 certifier)
 constexpr int kTcMaxSlots = 16;    // tensor-core form: most operand tiles held in shared memory
 
 // Dynamic shared memory of the tensor-core form besides its ring of operand
