@@ -295,6 +295,8 @@ struct Plan {
     int seg_records = 0;
     int tc_k = 0, tc_slots = 0, tc_resident = 0;
     long long tc_total_tiles = 0;
+    long long tc_chunk_items = 0;      // tensor-core form: work items per draw pass
+    size_t tc_item_bytes = 0;          // tensor-core form: drawn-sample bytes per work item
     int d = 0, n = 0, ngrids = 0;
     long long total_recs = 0;
     size_t grid_bytes = 0, hist_bytes = 0, dyn_smem = 0;
@@ -404,7 +406,7 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
         return QT_OK;
     }
     if (P.form == kTcRecheck) {
-        // one CTA of 13 warps per SM owns the 512 TMEM columns (two 256-column
+        // one CTA of 16 warps per SM owns the 512 TMEM columns (four 128-column
         // accumulators); the operand tiles take what the pipeline's buffers
         // leave of the shared memory, at most 16 tiles
         P.tc_k = P.dm <= 4 ? 16 : 32;
@@ -416,10 +418,15 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
         int tmax = 0;
         for (int k = 0; k < n; ++k) tmax = std::max(tmax, P.grids[k].tc_tiles + P.grids[k + 1].tc_tiles);
         P.tc_resident = tmax <= P.tc_slots;
+        // resident tiles take only the slots they need: the rest of the unified
+        // L1/shared memory caches the FP32 records that the certifiers re-score
+        if (P.tc_resident) P.tc_slots = std::max(2, tmax);
         P.S = 1;
         P.block = kTcThreads;
         P.tile = kTcTileM;
         P.grid_bytes = (size_t)fixed + (size_t)P.tc_slots * tile_bytes;
+        // the draw pass writes the samples of up to 2 GiB worth of work items at a time
+        P.tc_item_bytes = (size_t)(tc_item_op_bytes(P.tc_k) + tc_item_cert_bytes(P.dm));
         P.hist_bytes = 0;
         P.dyn_smem = P.grid_bytes;
         P.layers.resize(n);
@@ -445,6 +452,7 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
             coff += (long long)L.NA * L.NB;
         }
         P.total_items = item;
+        P.tc_chunk_items = std::max<long long>(1, std::min<long long>(P.total_items, (2ll << 30) / (long long)P.tc_item_bytes));
         P.count_entries = coff;
         return QT_OK;
     }
@@ -538,7 +546,7 @@ qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long
                           const qt_options* o, int source, void* dparams_f, void* dparams_d, const void* hparams_f,
                           const void* hparams_d, size_t pcount, void* dlayers, void* dgrids, const void* hlayers,
                           const void* hgrids, void* drec32, void* drec64, DevStatus* dstatus, cudaStream_t st,
-                          void* dtiles)
+                          void* dtiles, void* dtcitems)
 {
     QT_CUDA(cudaMemcpyAsync(dparams_f, hparams_f, pcount * 4, cudaMemcpyHostToDevice, st));
     QT_CUDA(cudaMemcpyAsync(dparams_d, hparams_d, pcount * 8, cudaMemcpyHostToDevice, st));
@@ -621,9 +629,23 @@ qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long
     // event nodes to be recorded at every replay
     const unsigned evflags = stream_is_capturing(st) ? cudaEventRecordExternal : cudaEventRecordDefault;
     QT_CUDA(cudaEventRecordWithFlags(ctx->ev_k0, st, evflags));
-    cudaError_t e = forward_launch(P.form, P.dm, P.S, P.streamed, fp, P.block, (int)P.dyn_smem, ctx->num_sms,
-                                   &blocks_per_sm, st);
-    if (e != cudaSuccess) return fail(ctx, QT_ECUDA, "forward kernel launch: %s", cudaGetErrorString(e));
+    if (P.form == kTcRecheck) {
+        // draw pass and tensor-core pass, chunk by chunk of work items
+        fp.tc_items = (unsigned char*)dtcitems;
+        for (long long lo = 0; lo < P.total_items; lo += P.tc_chunk_items) {
+            fp.item_lo = lo;
+            fp.item_hi = std::min(P.total_items, lo + P.tc_chunk_items);
+            cudaError_t e = launch_tc_draw(P.dm, fp, st);
+            if (e != cudaSuccess) return fail(ctx, QT_ECUDA, "draw pass launch: %s", cudaGetErrorString(e));
+            e = forward_launch(P.form, P.dm, P.S, P.streamed, fp, P.block, (int)P.dyn_smem, ctx->num_sms,
+                               &blocks_per_sm, st);
+            if (e != cudaSuccess) return fail(ctx, QT_ECUDA, "forward kernel launch: %s", cudaGetErrorString(e));
+        }
+    } else {
+        cudaError_t e = forward_launch(P.form, P.dm, P.S, P.streamed, fp, P.block, (int)P.dyn_smem, ctx->num_sms,
+                                       &blocks_per_sm, st);
+        if (e != cudaSuccess) return fail(ctx, QT_ECUDA, "forward kernel launch: %s", cudaGetErrorString(e));
+    }
     QT_CUDA(cudaEventRecordWithFlags(ctx->ev_k1, st, evflags));
     ctx->timed = true;
     return QT_OK;
@@ -683,8 +705,10 @@ qt_status run_plan(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long M, uns
     }
     if ((s = dev_get(ctx, (tag + "status").c_str(), sizeof(DevStatus), &dstatus))) return s;
     void* dtiles = nullptr;
+    void* dtcitems = nullptr;
     if (P.form == kTcRecheck &&
-        (s = dev_get(ctx, (tag + "tctiles").c_str(), (size_t)P.tc_total_tiles * kTcTileN * P.tc_k * 2, &dtiles)))
+        ((s = dev_get(ctx, (tag + "tctiles").c_str(), (size_t)P.tc_total_tiles * kTcTileN * P.tc_k * 2, &dtiles)) ||
+         (s = dev_get(ctx, (tag + "tcitems").c_str(), (size_t)P.tc_chunk_items * P.tc_item_bytes, &dtcitems))))
         return s;
     void *hlayers, *hgrids, *hpf, *hpd;
     if ((s = host_get(ctx, (tag + "layers").c_str(), sizeof(LayerDesc) * P.layers.size(), &hlayers))) return s;
@@ -708,7 +732,7 @@ qt_status run_plan(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long M, uns
     ctx->status_buf = dstatus;
     if (!use_graph) {
         s = enqueue_forward(ctx, P, io, M, seed, o, source, dpf, dpd, hpf, hpd, pbytes, dlayers, dgrids, hlayers,
-                            hgrids, drec32, drec64, (DevStatus*)dstatus, st, dtiles);
+                            hgrids, drec32, drec64, (DevStatus*)dstatus, st, dtiles, dtcitems);
         if (s) return s;
     } else {
         // graph key: everything the enqueued work depends on
@@ -735,7 +759,7 @@ qt_status run_plan(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long M, uns
             QT_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
             qt_status es = enqueue_forward(ctx, P, io, M, seed, o, source, dpf, dpd, hpf, hpd, pbytes, dlayers,
                                            dgrids, hlayers, hgrids, drec32, drec64, (DevStatus*)dstatus,
-                                           ctx->cap_stream, dtiles);
+                                           ctx->cap_stream, dtiles, dtcitems);
             cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
             if (es != QT_OK || ee != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);

@@ -306,9 +306,10 @@ namespace {
 constexpr int kEpiWarps = 8;       // warps 0-7: epilogue warpgroups 0 and 1
 constexpr int kMmaWarp0 = 8;       // warps 8, 9: MMAs for epilogue warpgroups 0, 1
 constexpr int kLoadWarp = 10;      // warp 10: bulk copies of the operand tiles
-constexpr int kCertWarp0 = 11;     // warps 11-14: draw, certify, recheck, count
+constexpr int kOpWarp = 11;        // warp 11: bulk copies of the drawn samples of each item
+constexpr int kCertWarp0 = 12;     // warps 12-15: certify, recheck, count
 constexpr int kHalfN = kTcTileN / 2;   // columns of one accumulator (MMA N)
-static_assert(kTcThreads == 15 * 32, "role layout");
+static_assert(kTcThreads == 16 * 32, "role layout");
 
 // What a certifier warp needs of the layer of an item (shared memory, one per
 // warp and operand slot, plus one for the layer of its draws).
@@ -319,6 +320,97 @@ struct SlotLayer {
 
 }  // namespace
 
+// Draw pass of the tensor-core form: one CTA of 128 threads per work item of
+// [item_lo, item_hi).  Thread t draws sample t of the item (Algorithm III, the
+// pair (X_k, X_{k+1}) of the AR(1) step), centres it on both grids and writes
+// the FP16 operand rows of both grids ([a_hi (DM), a_hi (DM), a_lo (DM), 1, 1],
+// a = -2 sigma (x - mu), core-matrix layout) and the centred FP32 coordinates
+// with their norm (sign bit set when a coordinate leaves the FP16 range).
+template <int DM, int KT>
+__global__ void __launch_bounds__(kTcTileM) tc_draw_kernel(const ForwardParams p)
+{
+    constexpr int K = 16 * KT;
+    constexpr int kOpBytes = kTcTileM * K * 2;
+    constexpr long long kItemOp = tc_item_op_bytes(K), kItemCert = tc_item_cert_bytes(DM);
+    __shared__ __align__(16) double s_par[param_count(DM)];
+    __shared__ float s_mu[2][DM];
+    __shared__ int s_k, s_exp[2];
+    __shared__ long long s_beg;
+    const int t = threadIdx.x;
+    const int d = p.d;
+    const long long item = p.item_lo + blockIdx.x;
+    if (t == 0) {
+        const int k = layer_of(p, item);
+        const LayerDesc& L = p.layers[k];
+        s_k = k;
+        s_beg = L.item_begin;
+        s_exp[0] = p.grids[L.gridA].tc_exp;
+        s_exp[1] = p.grids[L.gridB].tc_exp;
+#pragma unroll
+        for (int l = 0; l < DM; ++l) {
+            s_mu[0][l] = p.grids[L.gridA].mu[l];
+            s_mu[1][l] = p.grids[L.gridB].mu[l];
+        }
+    }
+    __syncthreads();
+    const int k = s_k;
+    if (p.source == kSampler) {
+        const int pc = param_count(d);
+        if (p.prec == 1) {
+            float* f = reinterpret_cast<float*>(s_par);
+            for (int e = t; e < pc; e += kTcTileM) f[e] = p.params_f[(long long)k * p.params_stride + e];
+        } else {
+            for (int e = t; e < pc; e += kTcTileM) s_par[e] = p.params_d[(long long)k * p.params_stride + e];
+        }
+    }
+    __syncthreads();
+    const unsigned long long mtile = (unsigned long long)(item - s_beg) * kTcTileM;
+    const unsigned long long ms = mtile + (unsigned long long)t;
+    const Centred<DM> cs = centred_sample_inl<DM>(p, reinterpret_cast<const float*>(s_par), s_par, s_mu[0], s_mu[1],
+                                                  k, ms < p.M ? ms : mtile);
+    unsigned char* dst = p.tc_items + (item - p.item_lo) * (kItemOp + kItemCert);
+    float* cert = reinterpret_cast<float*>(dst + kItemOp);
+#pragma unroll
+    for (int gr = 0; gr < 2; ++gr) {
+        const float* x = gr == 0 ? cs.xa : cs.yb;
+        const float A = gr == 0 ? cs.Aa : cs.Ab;
+        const float sg = ldexpf(1.0f, s_exp[gr]);
+        bool big = false;
+#pragma unroll
+        for (int l = 0; l < DM; ++l)
+            if (l < d) big = big || !(fabsf(sg * x[l]) <= 16384.0f);
+        uint32_t hi[DM], lo[DM];
+#pragma unroll
+        for (int l = 0; l < DM; ++l) {
+            const float v = (l < d && !big) ? sg * x[l] : 0.0f;
+            const __half h = __float2half_rn(v);
+            hi[l] = __half_as_ushort(h);
+            lo[l] = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+        }
+        const uint32_t one = __half_as_ushort(__float2half_rn(1.0f));
+        uint32_t w[K / 2];
+#pragma unroll
+        for (int q = 0; q < K; q += 2) {
+            uint32_t h2[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int c = q + u;
+                h2[u] = c < DM ? hi[c] : (c < 2 * DM ? hi[c - DM] : (c < 3 * DM ? lo[c - 2 * DM] : (c < 3 * DM + 2 ? one : 0u)));
+            }
+            w[q / 2] = h2[0] | (h2[1] << 16);
+        }
+        unsigned char* base = dst + gr * kOpBytes;
+#pragma unroll
+        for (int kb = 0; kb < K / 8; ++kb)
+            *reinterpret_cast<uint4*>(base + (((t >> 3) * (K / 8) + kb) * 64 + (t & 7) * 8) * 2) =
+                make_uint4(w[4 * kb], w[4 * kb + 1], w[4 * kb + 2], w[4 * kb + 3]);
+        float* cx = cert + gr * (DM + 1) * kTcTileM + t;
+#pragma unroll
+        for (int l = 0; l < DM; ++l) cx[l * kTcTileM] = x[l];
+        cx[DM * kTcTileM] = __int_as_float(__float_as_int(A) | (big ? (int)0x80000000 : 0));
+    }
+}
+
 template <int DM, int KT>
 __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const ForwardParams p)
 {
@@ -326,8 +418,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
     static_assert(3 * DM + 2 <= K, "operand row");
     constexpr int kTileBytes = kTcTileN * K * 2;
     constexpr int kOpBytes = kTcTileM * K * 2;
-    constexpr int PC = param_count(DM);
-    constexpr int PCpad = (PC + 1) / 2 * 2;
     constexpr int F = Rec32<DM>::kFloats;
     const float kInf = __int_as_float(0x7F800000);
     extern __shared__ __align__(128) unsigned char dsm_tc[];
@@ -338,8 +428,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
     __shared__ __align__(8) unsigned long long s_drain[2], s_ldone;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
-    __shared__ SlotLayer s_slot[4][3];
-    __shared__ float s_mu[4][2 * DM];
+    __shared__ SlotLayer s_slot[4][2];
+    __shared__ __align__(8) unsigned long long s_certdone[2];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -352,7 +442,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
     unsigned char* ops = ring + (size_t)RS * kTileBytes;                       // [item slot][grid] rows
     float* sst = reinterpret_cast<float*>(ops + 4 * kOpBytes);                 // [slot][grid][wg][5][128]
     float* scert = sst + 2 * 2 * 2 * 5 * kTcTileM;                             // [slot][grid][DM + 1][128]
-    double* sparam = reinterpret_cast<double*>(scert + 2 * 2 * (DM + 1) * kTcTileM);   // [cert warp][PCpad]
+    constexpr long long kItemOp = tc_item_op_bytes(K), kItemCert = tc_item_cert_bytes(DM);
+    static_assert(kItemOp == 2 * kOpBytes && kItemCert == 2 * (DM + 1) * kTcTileM * 4, "item layout");
     const uint32_t ring_u = smem_u32(ring), ops_u = smem_u32(ops);
 
     if (tid == 0) {
@@ -365,7 +456,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
             mbar_init(smem_u32(&s_accempty[a]), 128);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&s_opfull[b]), 128);
+            mbar_init(smem_u32(&s_opfull[b]), 1);
+            mbar_init(smem_u32(&s_certdone[b]), 128);
             mbar_init(smem_u32(&s_opempty[b]), 2);
             mbar_init(smem_u32(&s_stA[b]), 256);
             mbar_init(smem_u32(&s_stB[b]), 256);
@@ -415,8 +507,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                 ok = false;
             };
             for (long long n = 0; ok; ++n) {
-                const long long item = blockIdx.x + n * G;
-                if (item >= p.total_items || *abort_flag) break;
+                const long long item = p.item_lo + blockIdx.x + n * G;
+                if (item >= p.item_hi || *abort_flag) break;
                 if (item < lbeg || item >= lend) {
                     const LayerDesc& L = p.layers[layer_of(p, item)];
                     lbeg = L.item_begin;
@@ -526,8 +618,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                 int layers = 0, lastT = 0;
                 uint32_t tph = 0;              // per slot: parity of the next load's completion
                 for (long long n = 0;; ++n) {
-                    const long long item = blockIdx.x + n * G;
-                    if (item >= p.total_items || *abort_flag) break;
+                    const long long item = p.item_lo + blockIdx.x + n * G;
+                    if (item >= p.item_hi || *abort_flag) break;
                     if (item >= lbeg && item < lend) continue;
                     refresh(item);
                     if (layers > 0 &&
@@ -549,8 +641,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                 int li = 0, r = 0;
                 uint32_t rph = 0;              // parity of the ring's current lap
                 while (true) {
-                    const long long item = blockIdx.x + ln * G;
-                    if (item >= p.total_items || *abort_flag) break;
+                    const long long item = p.item_lo + blockIdx.x + ln * G;
+                    if (item >= p.item_hi || *abort_flag) break;
                     if (li == 0 && (item < lbeg || item >= lend)) refresh(item);
                     if (!mbar_wait_bounded(smem_u32(&s_tempty[r]), rph ^ 1u, p.spin_budget)) {
                         fail(25);
@@ -617,8 +709,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
             st[4 * kTcTileM] = __int_as_float(tr.bcs);
         };
         for (long long n = 0;; ++n) {
-            const long long item = blockIdx.x + n * G;
-            if (item >= p.total_items) break;
+            const long long item = p.item_lo + blockIdx.x + n * G;
+            if (item >= p.item_hi) break;
             if (__shfl_sync(0xFFFFFFFFu, *abort_flag, 0)) break;
             if (item < lbeg || item >= lend) {
                 const LayerDesc& L = p.layers[layer_of(p, item)];
@@ -653,14 +745,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
             }
             g += nT;
         }
+    } else if (warp == kOpWarp) {
+        // ================================================================ drawn samples
+        // item n's operand rows and centred samples go to slot n & 1 once the
+        // MMAs and the certifiers are done with item n - 2
+        if (lane == 0) {
+            long long n = 0;
+            for (;; ++n) {
+                const long long item = p.item_lo + blockIdx.x + n * G;
+                if (item >= p.item_hi || *abort_flag) break;
+                const int s = (int)(n & 1);
+                const uint32_t par = (uint32_t)((n >> 1) & 1) ^ 1u;
+                if (!mbar_wait_bounded(smem_u32(&s_opempty[s]), par, p.spin_budget) ||
+                    !mbar_wait_bounded(smem_u32(&s_certdone[s]), par, p.spin_budget)) {
+                    record_error(p.status, 4 /* QT_ETIMEOUT */, 27);
+                    *abort_flag = 1;
+                    break;
+                }
+                const unsigned char* src = p.tc_items + (item - p.item_lo) * (kItemOp + kItemCert);
+                const uint32_t bar = smem_u32(&s_opfull[s]);
+                mbar_arrive_expect_tx(bar, (uint32_t)(kItemOp + kItemCert));
+                bulk_g2s(ops_u + (uint32_t)(s * kItemOp), src, (uint32_t)kItemOp, bar);
+                bulk_g2s(smem_u32(scert) + (uint32_t)(s * kItemCert), src + kItemOp, (uint32_t)kItemCert, bar);
+            }
+            // the copies of the last two items land before the shared memory is released
+            for (long long q = n > 2 ? n - 2 : 0; q < n; ++q)
+                mbar_wait_bounded(smem_u32(&s_opfull[q & 1]), (uint32_t)((q >> 1) & 1), 1ll << 24);
+        }
     } else {
         // ================================================================ certifiers
         const int cw = warp - kCertWarp0;
         const int t = cw * 32 + lane;
-        double* wpar = sparam + cw * PCpad;      // this warp's copy of the parameters of its draws' layer
-        float* wmu = s_mu[cw];                    // and the centres of that layer's two grids
-        SlotLayer* sl = s_slot[cw];               // [0], [1]: layer of the item in each slot; [2]: of the draws
-        long long dbeg = 0, dend = 0;             // items of the draws' layer
+        SlotLayer* sl = s_slot[cw];               // layer of the item in each slot
+        long long lbeg = 0, lend = 0;
+        SlotLayer cur;
+        cur.k = -1;
         int slot_k[2] = {-1, -1};
         auto fail = [&](int where) {
             if (lane == 0) {
@@ -668,104 +787,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                 *abort_flag = 1;
             }
         };
-        // Row t of item ordinal n into operand slot s: draw, centre, split.
-        auto draw = [&](long long n, int s) {
-            const long long item = blockIdx.x + n * G;
-            if (item < dbeg || item >= dend) {
-                const int k = layer_of(p, item);
-                const LayerDesc& L = p.layers[k];
-                const GridInfo& GA = p.grids[L.gridA];
-                const GridInfo& GB = p.grids[L.gridB];
-                __syncwarp();
-                if (p.source == kSampler) {
-                    const int pc = param_count(d);
-                    if (p.prec == 1) {
-                        float* f = reinterpret_cast<float*>(wpar);
-                        for (int e = lane; e < pc; e += 32) f[e] = p.params_f[(long long)k * p.params_stride + e];
-                    } else {
-                        for (int e = lane; e < pc; e += 32) wpar[e] = p.params_d[(long long)k * p.params_stride + e];
-                    }
-                }
-                if (lane < DM) {
-                    wmu[lane] = GA.mu[lane];
-                    wmu[DM + lane] = GB.mu[lane];
-                }
-                if (lane == 0) {
-                    SlotLayer& D = sl[2];
-                    D.item_begin = L.item_begin;
-                    D.coff = L.coff;
-                    D.goffA = GA.goff;
-                    D.goffB = GB.goff;
-                    D.roffA = GA.roff;
-                    D.roffB = GB.roff;
-                    D.k = k;
-                    D.NA = L.NA;
-                    D.NB = L.NB;
-                    D.NpadA = GA.Npad;
-                    D.NpadB = GB.Npad;
-                    D.expA = GA.tc_exp;
-                    D.expB = GB.tc_exp;
-                }
-                __syncwarp();
-                dbeg = L.item_begin;
-                dend = dbeg + L.items;
-            }
-            const SlotLayer& D = sl[2];
-            if (slot_k[s] != D.k) {
-                if (lane == 0) sl[s] = D;
-                __syncwarp();
-                slot_k[s] = D.k;
-            }
-            const unsigned long long mtile = (unsigned long long)(item - D.item_begin) * kTcTileM;
-            const unsigned long long ms = mtile + (unsigned long long)t;
-            const Centred<DM> cs = centred_sample_inl<DM>(p, reinterpret_cast<const float*>(wpar), wpar, wmu,
-                                                          wmu + DM, D.k, ms < p.M ? ms : mtile);
-#pragma unroll
-            for (int gr = 0; gr < 2; ++gr) {
-                const float* x = gr == 0 ? cs.xa : cs.yb;
-                const float A = gr == 0 ? cs.Aa : cs.Ab;
-                const float sg = ldexpf(1.0f, gr == 0 ? D.expA : D.expB);
-                bool big = false;
-#pragma unroll
-                for (int l = 0; l < DM; ++l)
-                    if (l < d) big = big || !(fabsf(sg * x[l]) <= 16384.0f);
-                uint32_t hi[DM], lo[DM];
-#pragma unroll
-                for (int l = 0; l < DM; ++l) {
-                    const float v = (l < d && !big) ? sg * x[l] : 0.0f;
-                    const __half h = __float2half_rn(v);
-                    hi[l] = __half_as_ushort(h);
-                    lo[l] = __half_as_ushort(__float2half_rn(v - __half2float(h)));
-                }
-                const uint32_t one = __half_as_ushort(__float2half_rn(1.0f));
-                uint32_t w[K / 2];
-#pragma unroll
-                for (int q = 0; q < K; q += 2) {
-                    uint32_t h2[2];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int c = q + u;
-                        h2[u] = c < DM ? hi[c] : (c < 2 * DM ? hi[c - DM] : (c < 3 * DM ? lo[c - 2 * DM] : (c < 3 * DM + 2 ? one : 0u)));
-                    }
-                    w[q / 2] = h2[0] | (h2[1] << 16);
-                }
-                unsigned char* base = ops + (s * 2 + gr) * kOpBytes;
-#pragma unroll
-                for (int kb = 0; kb < K / 8; ++kb)
-                    *reinterpret_cast<uint4*>(base + (((t >> 3) * (K / 8) + kb) * 64 + (t & 7) * 8) * 2) =
-                        make_uint4(w[4 * kb], w[4 * kb + 1], w[4 * kb + 2], w[4 * kb + 3]);
-                float* cx = scert + (s * 2 + gr) * (DM + 1) * kTcTileM + t;
-#pragma unroll
-                for (int l = 0; l < DM; ++l) cx[l * kTcTileM] = x[l];
-                cx[DM * kTcTileM] = __int_as_float(__float_as_int(A) | (big ? (int)0x80000000 : 0));
-            }
-        };
         // Merge the warpgroups' chunk states of row t, re-score the best chunk
-        // in FP32 (and the second one when the certificate needs it) and
-        // certify; returns the cell, sets `need`.
-        auto certify = [&](int s, int gr, const SlotLayer& S, bool valid, bool& need) -> int {
+        // in FP32 and try the certificate (first pass, straight-line code, so
+        // that the two grids' passes overlap); then, where the certificate
+        // needs it, re-score the second chunk too and finish.
+        struct Pass {
+            float x[DM];
+            float A, rest, v1, inv_sg, best, in2, r1;
+            int idx, mbc, c1, nch, why;
+            bool big, chunk_ok, tcok;
+            const float* recs;
+        };
+        auto first = [&](int s, int gr, const SlotLayer& S, Pass& c) {
             const int Npad = gr == 0 ? S.NpadA : S.NpadB;
-            const int Nown = gr == 0 ? S.NA : S.NB;
             const float* st = sst + (s * 2 + gr) * 2 * 5 * kTcTileM + t;
             float v0 = st[0], v1 = st[kTcTileM], v2 = st[5 * kTcTileM], v3 = st[6 * kTcTileM];
             int c0 = __float_as_int(st[3 * kTcTileM]), c1 = __float_as_int(st[4 * kTcTileM]);
@@ -776,45 +810,47 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
             pair_sort2(v0, c0, v2, c2);
             pair_sort2(v1, c1, v3, c3);
             pair_sort2(v1, c1, v2, c2);
-            rest = fminf(rest, fminf(v2, v3));
-            const int nch = Npad / kChunk;
+            c.rest = fminf(rest, fminf(v2, v3));
+            c.v1 = v1;
+            c.c1 = c1;
+            c.nch = Npad / kChunk;
             const float* cx = scert + (s * 2 + gr) * (DM + 1) * kTcTileM + t;
-            float x[DM];
 #pragma unroll
-            for (int l = 0; l < DM; ++l) x[l] = cx[l * kTcTileM];
+            for (int l = 0; l < DM; ++l) c.x[l] = cx[l * kTcTileM];
             const float Araw = cx[DM * kTcTileM];
-            const bool big = (__float_as_int(Araw) & (int)0x80000000) != 0;
-            const float A = fabsf(Araw);
-            const float inv_sg = ldexpf(1.0f, -(gr == 0 ? S.expA : S.expB));
-            const float* recs = p.rec32 + (gr == 0 ? S.roffA : S.roffB) * F;
-            const bool chunk_ok = c0 >= 0 && c0 < nch;
-            const int mbc = chunk_ok ? c0 : 0;
-            int idx;
-            float best, in2, r1;
-            cc_chunk<DM>(recs, mbc, x, idx, best, in2, r1);
-            // first: FP32 inside the best chunk, tensor-core scores outside it
-            int why = 0;
-            bool tcok = tc_certified(d, A, best, in2, fminf(v1, rest) * inv_sg * inv_sg, r1, inv_sg, why);
-            if (!tcok && why == 2 && c1 >= 0 && c1 < nch && c1 != mbc) {
+            c.big = (__float_as_int(Araw) & (int)0x80000000) != 0;
+            c.A = fabsf(Araw);
+            c.inv_sg = ldexpf(1.0f, -(gr == 0 ? S.expA : S.expB));
+            c.recs = p.rec32 + (gr == 0 ? S.roffA : S.roffB) * F;
+            c.chunk_ok = c0 >= 0 && c0 < c.nch;
+            c.mbc = c.chunk_ok ? c0 : 0;
+            cc_chunk<DM>(c.recs, c.mbc, c.x, c.idx, c.best, c.in2, c.r1);
+            // FP32 inside the best chunk, tensor-core scores outside it
+            c.why = 0;
+            c.tcok = tc_certified(d, c.A, c.best, c.in2, fminf(c.v1, c.rest) * c.inv_sg * c.inv_sg, c.r1, c.inv_sg,
+                                  c.why);
+        };
+        auto finish = [&](Pass& c, int Nown, bool valid, bool& need) -> int {
+            if (!c.tcok && c.why == 2 && c.c1 >= 0 && c.c1 < c.nch && c.c1 != c.mbc) {
                 // the second chunk competes: FP32 inside both, tensor-core scores outside
                 int idx2;
                 float best2, S12, r12;
-                cc_chunk<DM>(recs, c1, x, idx2, best2, S12, r12);
-                if (best2 < best || (best2 == best && idx2 < idx)) {
-                    in2 = fminf(S12, best);
-                    best = best2;
-                    idx = idx2;
-                    r1 = r12;
+                cc_chunk<DM>(c.recs, c.c1, c.x, idx2, best2, S12, r12);
+                if (best2 < c.best || (best2 == c.best && idx2 < c.idx)) {
+                    c.in2 = fminf(S12, c.best);
+                    c.best = best2;
+                    c.idx = idx2;
+                    c.r1 = r12;
                 } else {
-                    in2 = fminf(in2, best2);
+                    c.in2 = fminf(c.in2, best2);
                 }
-                tcok = tc_certified(d, A, best, in2, rest * inv_sg * inv_sg, r1, inv_sg, why);
+                c.tcok = tc_certified(d, c.A, c.best, c.in2, c.rest * c.inv_sg * c.inv_sg, c.r1, c.inv_sg, c.why);
             }
-            const bool rng_ok = chunk_ok && idx < Nown && !big;
-            const bool cert = tcok && rng_ok;
-            if (valid && !cert) atomicAdd(&p.status->spare[!rng_ok ? 3 : why], 1ull);
+            const bool rng_ok = c.chunk_ok && c.idx < Nown && !c.big;
+            const bool cert = c.tcok && rng_ok;
+            if (valid && !cert) atomicAdd(&p.status->spare[!rng_ok ? 3 : c.why], 1ull);
             need = valid && !cert;
-            return idx;
+            return c.idx;
         };
         // exact window search of the lanes in `need` (the whole warp takes part)
         auto recheck = [&](int s, int gr, const SlotLayer& S, unsigned long long ms, bool need, int& cell) {
@@ -842,44 +878,64 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                 if (lane == 0) atomicAdd(&p.status->rechecks, 1ull);
             }
         };
-        if (blockIdx.x < p.total_items) {
-            draw(0, 0);
-            fence_proxy_async();
-            mbar_arrive(smem_u32(&s_opfull[0]));
-        }
         for (long long n = 0;; ++n) {
-            const long long item = blockIdx.x + n * G;
-            if (item >= p.total_items) break;
+            const long long item = p.item_lo + blockIdx.x + n * G;
+            if (item >= p.item_hi) break;
             if (__shfl_sync(0xFFFFFFFFu, *abort_flag, 0)) break;
-            // operands of the next item: its slot is free once item n - 1's MMAs are done
-            if (item + G < p.total_items) {
-                const int s1 = (int)((n + 1) & 1);
-                if (!warp_wait(smem_u32(&s_opempty[s1]), (uint32_t)(((n + 1) >> 1) & 1) ^ 1u, p.spin_budget)) {
-                    fail(27);
-                    break;
-                }
-                draw(n + 1, s1);
-                fence_proxy_async();
-                mbar_arrive(smem_u32(&s_opfull[s1]));
-            }
             const int s = (int)(n & 1);
+            if (item < lbeg || item >= lend) {
+                const int k = layer_of(p, item);
+                const LayerDesc& L = p.layers[k];
+                const GridInfo& GA = p.grids[L.gridA];
+                const GridInfo& GB = p.grids[L.gridB];
+                cur.item_begin = L.item_begin;
+                cur.coff = L.coff;
+                cur.goffA = GA.goff;
+                cur.goffB = GB.goff;
+                cur.roffA = GA.roff;
+                cur.roffB = GB.roff;
+                cur.k = k;
+                cur.NA = L.NA;
+                cur.NB = L.NB;
+                cur.NpadA = GA.Npad;
+                cur.NpadB = GB.Npad;
+                cur.expA = GA.tc_exp;
+                cur.expB = GB.tc_exp;
+                lbeg = L.item_begin;
+                lend = lbeg + L.items;
+            }
+            if (slot_k[s] != cur.k) {
+                __syncwarp();
+                if (lane == 0) sl[s] = cur;
+                __syncwarp();
+                slot_k[s] = cur.k;
+            }
             const SlotLayer& S = sl[s];
             const unsigned long long ms = (unsigned long long)(item - S.item_begin) * kTcTileM + (unsigned long long)t;
             const bool valid = ms < p.M;
             bool needA = false, needB = false;
+            // the centred samples of this item have landed (the MMAs waited for them too)
+            if (!warp_wait(smem_u32(&s_opfull[s]), (uint32_t)((n >> 1) & 1), p.spin_budget)) {
+                fail(30);
+                break;
+            }
             if (!warp_wait(smem_u32(&s_stA[s]), (uint32_t)((n >> 1) & 1), p.spin_budget)) {
                 fail(28);
                 break;
             }
-            int ci = certify(s, 0, S, valid, needA);
             if (!warp_wait(smem_u32(&s_stB[s]), (uint32_t)((n >> 1) & 1), p.spin_budget)) {
                 fail(29);
                 break;
             }
-            int cj = certify(s, 1, S, valid, needB);
+            Pass pa, pb;
+            first(s, 0, S, pa);
+            first(s, 1, S, pb);
             mbar_arrive(smem_u32(&s_stempty[s]));
+            int ci = finish(pa, S.NA, valid, needA);
+            int cj = finish(pb, S.NB, valid, needB);
             recheck(s, 0, S, ms, needA, ci);
             recheck(s, 1, S, ms, needB, cj);
+            mbar_arrive(smem_u32(&s_certdone[s]));
             // ---- counters p^k_ij
             if (valid) {
                 if ((unsigned)ci >= (unsigned)S.NA || (unsigned)cj >= (unsigned)S.NB) {
@@ -937,10 +993,29 @@ static cudaError_t launch_tc(const ForwardParams& p, int dyn, int num_sms, int* 
     if (p.tc_slots < 2 || p.tc_slots > kTcMaxSlots) return cudaErrorInvalidValue;
     *bps = b;
     long long grid = (long long)num_sms * b;
-    if (grid > p.total_items) grid = p.total_items;
+    if (grid > p.item_hi - p.item_lo) grid = p.item_hi - p.item_lo;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, kTcThreads, dyn, st>>>(p);
     return cudaGetLastError();
+}
+
+template <int DM, int KT>
+static cudaError_t launch_draw(const ForwardParams& p, cudaStream_t st)
+{
+    const long long n = p.item_hi - p.item_lo;
+    if (n < 1) return cudaSuccess;
+    tc_draw_kernel<DM, KT><<<(unsigned)n, kTcTileM, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_draw(int dm, const ForwardParams& p, cudaStream_t st)
+{
+    if (dm == 2) return launch_draw<2, 1>(p, st);
+    if (dm == 4) return launch_draw<4, 1>(p, st);
+    if (dm == 6) return launch_draw<6, 2>(p, st);
+    if (dm == 8) return launch_draw<8, 2>(p, st);
+    if (dm == 10) return launch_draw<10, 2>(p, st);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tc_forward(int dm, const ForwardParams& p, int dyn, int num_sms, int* bps, cudaStream_t st)

@@ -49,17 +49,23 @@ struct GridInfo {
 
 constexpr int kTcTileN = 256;      // grid points per tensor-core operand tile (MMA N)
 constexpr int kTcTileM = 128;      // samples per tensor-core work item (MMA M)
-constexpr int kTcThreads = 480;    // tensor-core form: 15 warps (8 epilogue, 2 MMA, loader, 4 certifier)
+constexpr int kTcThreads = 512;    // tensor-core form: 16 warps (8 epilogue, 2 MMA, 2 loaders, 4 certifier)
 constexpr int kTcMaxSlots = 16;    // tensor-core form: most operand tiles held in shared memory
+
+// Bytes of one work item's drawn samples in the tensor-core form, as the draw
+// pass writes them and the forward kernel copies them: the FP16 operand rows
+// of both grids (128 x K each, core-matrix layout), then the centred FP32
+// coordinates and norms ([grid][dm + 1][128]).
+__host__ __device__ constexpr long long tc_item_op_bytes(int K) { return 2ll * kTcTileM * K * 2; }
+__host__ __device__ constexpr long long tc_item_cert_bytes(int dm) { return 2ll * (dm + 1) * kTcTileM * 4; }
 
 // Dynamic shared memory of the tensor-core form besides its ring of operand
 // tiles (dimension class dm, K columns per operand row).
 __host__ __device__ constexpr long long tc_fixed_smem(int dm, int K)
 {
-    return 4ll * kTcTileM * K * 2                            // sample operands: 2 items x 2 grids
+    return 2 * tc_item_op_bytes(K)                           // sample operands: 2 items
            + 2ll * 2 * 2 * 5 * kTcTileM * 4                  // chunk states: 2 items x 2 grids x 2 warpgroups x 5
-           + 2ll * 2 * (dm + 1) * kTcTileM * 4               // centred samples: 2 items x 2 grids x (dm + 1)
-           + 4ll * ((2 * dm + 3 * dm * dm + 1) / 2 * 2) * 8; // layer parameters, one copy per certifier warp
+           + 2 * tc_item_cert_bytes(dm);                     // centred samples: 2 items
 }
 
 struct ForwardParams {
@@ -106,6 +112,8 @@ struct ForwardParams {
     int32_t tc_k;                  // 16 or 32
     int32_t tc_slots;              // ring slots of operand tiles in shared memory
     int32_t tc_resident;           // 1: both grids' tiles stay in shared memory for the layer
+    long long item_lo, item_hi;    // tensor-core form: work items [item_lo, item_hi) of this launch
+    unsigned char* tc_items;       // tensor-core form: drawn samples of those items, tc_item_*_bytes each
     // learned router + Elkan certificate
     const float* rt_params;        // MLP parameters, packed W1, b1, W2, b2, W3, b3
     const float* rt_linv;          // [n+1][d][d] FP32 inverse Cholesky factors (whitening)
