@@ -68,8 +68,9 @@ def grid_method(model):
 
 def default_form(model, B):
     # the fastest certified form measured for each dimension class: the FP32 screen
-    # (exact through its certificate) up to d = 8, the tensor-core screen for d = 10
-    return B.FORM_TC_RECHECK if model.d >= 10 else B.FORM_F32_RECHECK
+    # for d <= 2, the tensor-core screen for 3 <= d <= 10 (both exact through their
+    # certificates)
+    return B.FORM_TC_RECHECK if 3 <= model.d <= 10 else B.FORM_F32_RECHECK
 
 
 def plain_form(model, B):
@@ -85,6 +86,27 @@ def flops_per_sample_layer(model):
     N = np.asarray(model.N, dtype=np.float64)
     cand = np.sum(N[:-1] + N[1:]) / model.n
     return float(cand * (2 * model.d + 1))
+
+
+def tc_flops_per_sample_layer(model):
+    """Useful tensor-core work of the tensor-core screen: per candidate one dot
+    product of the 3d + 2 operand columns that carry data (FP16 head/tail split of
+    sample and grid point, plus the squared norm), 2 flops each."""
+    N = np.asarray(model.N, dtype=np.float64)
+    cand = np.sum(N[:-1] + N[1:]) / model.n
+    return float(cand * (3 * model.d + 2) * 2)
+
+
+def tc_launches_per_step(model):
+    """Kernels the tensor-core form launches per step: record and operand-tile
+    preparation, then a draw pass and a forward pass per chunk of work items (the
+    library draws up to 2 GiB of samples per chunk)."""
+    dm = 2 if model.d <= 2 else (4 if model.d <= 4 else (6 if model.d <= 6 else (8 if model.d <= 8 else 10)))
+    K = 16 if dm <= 4 else 32
+    item_bytes = 2 * 128 * K * 2 + 2 * (dm + 1) * 128 * 4
+    items = model.n * ((model.M + 127) // 128)
+    chunk = max(1, min(items, (2 << 30) // item_bytes))
+    return 2 + 2 * ((items + chunk - 1) // chunk)
 
 
 def replica_seed(model, rank: int) -> int:
@@ -364,6 +386,17 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel_ms": kmean,
                 "peak_basis": f"FP32 FMA lanes: {n_sm} SMs x {FP32_LANES_PER_SM} x 2 flops x {sm_max:.0f} MHz"}
+    if form == B.FORM_TC_RECHECK:
+        # a contraction on the tensor cores: FP16 MMAs against the measured dense
+        # bf16 rate (the same rate as FP16 on this part), the sustained figure for
+        # a kernel timed inside a long step; the time spans the draw passes too
+        tpeak = peaks.get("bf16_tflops_sustained", 1700.0)
+        tach = tc_flops_per_sample_layer(model) * units / world / (kmean / 1e3) / 1e12
+        roofline = {"bound": "tensor", "achieved": tach, "peak": tpeak, "unit": "TFLOP/s", "frac": tach / tpeak,
+                    "traffic": traffic, "kernel_ms": kmean,
+                    "peak_basis": "measured dense bf16 GEMM, sustained (of measured)"
+                    if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)",
+                    "fp32_equivalent_tflops": achieved}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -384,7 +417,7 @@ def main():
                            "uncertified_by_cause": diag if form == B.FORM_TC_RECHECK else None,
                            "router": router_info,
                            "candidates_per_search": (cand / (2 * units)) if router else None},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (tc_launches_per_step(model) if form == B.FORM_TC_RECHECK else 2) * args.steps,
                 "clocks": clocks, "plain": plain}
         print(json.dumps(line), flush=True)
     ctx.close()

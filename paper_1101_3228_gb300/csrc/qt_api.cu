@@ -328,7 +328,9 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
     P.n = n;
     P.dm = dm_for(d);
     int form = o->form;
-    if (form == QT_FORM_AUTO) form = QT_FORM_F32_RECHECK;
+    // automatic choice: the fastest certified form measured on GB300 -- the
+    // tensor-core screen for 3 <= d <= 10, the FP32 screen otherwise
+    if (form == QT_FORM_AUTO) form = (d >= 3 && d <= 10) ? QT_FORM_TC_RECHECK : QT_FORM_F32_RECHECK;
     if (form != QT_FORM_PLAIN_F64 && form != QT_FORM_F32_RECHECK && form != QT_FORM_TC_RECHECK &&
         form != QT_FORM_ROUTER_CERT)
         return fail(ctx, QT_EINVAL, "unknown search form %d", form);

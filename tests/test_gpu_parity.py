@@ -122,9 +122,9 @@ def test_streamed_timeout_is_reported(ctx, B):
     model = _model("ar8", M=600, n=2, N=4000)
     g = _dev(W.layer_grids(model, samples=12000, iters=2))
     with pytest.raises(B.QtError) as e:
-        ctx.transitions(model, g, model.M, model.seed, B.options(spin_budget=-1))
+        ctx.transitions(model, g, model.M, model.seed, B.options(form=B.FORM_F32_RECHECK, spin_budget=-1))
     assert e.value.status == B.QT_ETIMEOUT
-    counts, _, _ = ctx.transitions(model, g, model.M, model.seed)
+    counts, _, _ = ctx.transitions(model, g, model.M, model.seed, B.options(form=B.FORM_F32_RECHECK))
     assert int(counts.sum()) == model.n * model.M
 
 
@@ -145,6 +145,28 @@ def test_counts_bit_exact_tensor_core(ctx, B, name, N, M, n):
     for k in range(model.n):
         np.testing.assert_array_equal(got[k], ref[k], err_msg=f"layer {k}")
     assert stats.device_status == 0 and stats.form_used == B.FORM_TC_RECHECK
+
+
+@pytest.mark.parametrize("name,N", [("ar8", 4000), ("basket4", 0)])
+def test_tensor_core_dump_samples_and_cells(ctx, B, name, N):
+    """Tensor-core form (automatic choice for these d): strided samples of every layer and
+    their cells against the oracle's sampler and exact search, one by one."""
+    model = _model(name, M=40000, n=3, N=N) if N else _model(name, M=40000, n=3)
+    g = W.layer_grids(model, samples=max(20000, 3 * int(model.N[-1])), iters=3)
+    stride = 97
+    cnt = (model.M + stride - 1) // stride
+    counts, stats, dump = ctx.transitions(model, _dev(g), model.M, model.seed, B.options(), dump_count=cnt,
+                                          dump_stride=stride)
+    assert stats.form_used == B.FORM_TC_RECHECK and stats.device_status == 0
+    off = model.offsets()
+    for k in range(model.n):
+        X, Y = oracle.sample_pairs(model.d, oracle.PREC_F32, model.seed, k, 0, model.M, model.m[k], model.L[k],
+                                   model.A[k], model.b[k], model.T[k])
+        X, Y = X[::stride], Y[::stride]
+        np.testing.assert_array_equal(dump["X"][k].cpu().numpy(), X)
+        np.testing.assert_array_equal(dump["Y"][k].cpu().numpy(), Y)
+        np.testing.assert_array_equal(dump["i"][k].cpu().numpy(), oracle.nearest(g[off[k]:off[k + 1]], X))
+        np.testing.assert_array_equal(dump["j"][k].cpu().numpy(), oracle.nearest(g[off[k + 1]:off[k + 2]], Y))
 
 
 def test_tensor_core_adversarial_near_ties(ctx, B):
@@ -230,7 +252,8 @@ def test_adversarial_near_ties_force_rechecks(ctx, B):
         Y = np.concatenate([W.boundary_samples(gB, 3000, seed=3),
                             W.boundary_samples(gB, 3000, seed=4, jitter=1e-9),
                             rng.standard_normal((2000, d))])
-        counts, stats, ii, jj = ctx.counts_from_samples(_dev(gA), _dev(gB), _dev(X), _dev(Y), want_cells=True)
+        counts, stats, ii, jj = ctx.counts_from_samples(_dev(gA), _dev(gB), _dev(X), _dev(Y),
+                                                        B.options(form=B.FORM_F32_RECHECK), want_cells=True)
         np.testing.assert_array_equal(ii.cpu().numpy(), oracle.nearest(gA, X))
         np.testing.assert_array_equal(jj.cpu().numpy(), oracle.nearest(gB, Y))
         np.testing.assert_array_equal(counts.cpu().numpy(), oracle.counts_from_samples(gA, gB, X, Y))
