@@ -409,10 +409,12 @@ def test_full_size_ou2_sampled_outputs(ctx, B):
 # ------------------------------------------------------------------ failure paths (host-made, no GPU fault)
 
 def test_bounded_wait_timeout_is_reported_and_context_survives(ctx, B):
+    """The plain FP64 form stages its grids by bulk copy and waits on an mbarrier
+    (the resident FP32 screen stages them with plain loads and has no such wait)."""
     model = _model("ou2", M=3000, n=2, N=64)
     g = _dev(_grids(model))
     with pytest.raises(B.QtError) as e:
-        ctx.transitions(model, g, model.M, model.seed, B.options(spin_budget=-1))
+        ctx.transitions(model, g, model.M, model.seed, B.options(form=B.FORM_PLAIN_F64, spin_budget=-1))
     assert e.value.status == B.QT_ETIMEOUT
     counts, stats, _ = ctx.transitions(model, g, model.M, model.seed)
     ref = oracle.transitions(model, g.cpu().numpy(), model.M, model.seed, oracle.PREC_F32)
