@@ -66,32 +66,23 @@ __device__ __forceinline__ void tc_commit(uint32_t bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32])
+// Minima of four consecutive 16-column chunks of this thread's accumulator row
+// (columns taddr .. taddr + 63): tcgen05.ld.red loads 16 columns and returns
+// their minimum; the loaded values themselves go to scratch registers local to
+// this block, which also waits for the loads, so nothing outside it can touch
+// registers the loads are still writing.
+__device__ __forceinline__ void tc_chunk_min4(uint32_t taddr, float& m0, float& m1, float& m2, float& m3)
 {
-    uint32_t r[32];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
+        "{\n\t.reg .f32 a<16>, b<16>, c<16>, e<16>;\n\t"
+        "tcgen05.ld.red.sync.aligned.32x32b.x16.min.f32 {a0,a1,a2,a3,a4,a5,a6,a7,a8,a9,a10,a11,a12,a13,a14,a15}, %0, [%4];\n\t"
+        "tcgen05.ld.red.sync.aligned.32x32b.x16.min.f32 {b0,b1,b2,b3,b4,b5,b6,b7,b8,b9,b10,b11,b12,b13,b14,b15}, %1, [%5];\n\t"
+        "tcgen05.ld.red.sync.aligned.32x32b.x16.min.f32 {c0,c1,c2,c3,c4,c5,c6,c7,c8,c9,c10,c11,c12,c13,c14,c15}, %2, [%6];\n\t"
+        "tcgen05.ld.red.sync.aligned.32x32b.x16.min.f32 {e0,e1,e2,e3,e4,e5,e6,e7,e8,e9,e10,e11,e12,e13,e14,e15}, %3, [%7];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n\t}"
+        : "=f"(m0), "=f"(m1), "=f"(m2), "=f"(m3)
+        : "r"(taddr), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u)
         : "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ float min16(const float* v)
-{
-    const float a = min3f(v[0], v[1], v[2]);
-    const float b = min3f(v[3], v[4], v[5]);
-    const float c = min3f(v[6], v[7], v[8]);
-    const float e = min3f(v[9], v[10], v[11]);
-    const float f = min3f(v[12], v[13], v[14]);
-    return min3f(min3f(a, b, c), min3f(e, f, v[15]), __int_as_float(0x7F800000));
 }
 
 // Bound on |tensor-core score - exact score| in FP32-score units for a grid
@@ -685,15 +676,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                 tc_fence_after();
 #pragma unroll
                 for (int q = 0; q < kHalfN / 64; ++q) {
-                    float va[32], vb[32];
-                    tc_ld32(trow + (uint32_t)(acc * kHalfN + q * 64), va);
-                    tc_ld32(trow + (uint32_t)(acc * kHalfN + q * 64 + 32), vb);
-                    tc_wait_ld();
+                    float m0, m1, m2, m3;
+                    tc_chunk_min4(trow + (uint32_t)(acc * kHalfN + q * 64), m0, m1, m2, m3);
                     const int c0 = lt * (kTcTileN / kChunk) + h * (kHalfN / kChunk) + q * 4;
-                    tr.add(min16(va), c0);
-                    tr.add(min16(va + 16), c0 + 1);
-                    tr.add(min16(vb), c0 + 2);
-                    tr.add(min16(vb + 16), c0 + 3);
+                    tr.add(m0, c0);
+                    tr.add(m1, c0 + 1);
+                    tr.add(m2, c0 + 2);
+                    tr.add(m3, c0 + 3);
                 }
                 tc_fence_before();
                 mbar_arrive(smem_u32(&s_accempty[acc]));
