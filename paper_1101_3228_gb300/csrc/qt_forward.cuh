@@ -370,6 +370,25 @@ __device__ __forceinline__ void resolve_one(const float* __restrict__ recs, int 
     resolve_chunk<DM>(recs, bc, bc, x, B1, idx, S1, r1);
 }
 
+
+// ---- packed FP32 pairs (fma.rn.f32x2: two independent FP32 FMAs, each rounded
+// to nearest, so each lane's result is bit-identical to the scalar FMA)
+__device__ __forceinline__ uint64_t pack2(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t v, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t x, uint64_t c, uint64_t a)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(x), "l"(c), "l"(a));
+    return r;
+}
 template <int V>
 __device__ __forceinline__ void load_pair(const float4* __restrict__ r4, int j, float4 (&a)[V], float4 (&b)[V])
 {
@@ -390,6 +409,13 @@ __device__ __forceinline__ void screen_scan(const float* __restrict__ recs, int 
     constexpr int V = Rec32<DM>::kVec;
     const float4* r4 = reinterpret_cast<const float4*>(recs);
     const int last = nchunk * kChunk - 2;
+    // samples 2p and 2p + 1 share one packed FMA per record element: their
+    // coordinates side by side, the record's element broadcast to both lanes
+    uint64_t xp[S / 2 > 0 ? S / 2 : 1][DM];
+#pragma unroll
+    for (int sp = 0; sp < S / 2; ++sp)
+#pragma unroll
+        for (int l = 0; l < DM; ++l) xp[sp][l] = pack2(xs[2 * sp][l], xs[2 * sp + 1][l]);
     float4 na[V], nb[V];
     load_pair<V>(r4, 0, na, nb);
     for (int c = 0; c < nchunk; ++c) {
@@ -408,8 +434,30 @@ __device__ __forceinline__ void screen_scan(const float* __restrict__ recs, int 
             load_pair<V>(r4, jn, na, nb);
             const float* ra = reinterpret_cast<const float*>(ca);
             const float* rb = reinterpret_cast<const float*>(cb);
+            if constexpr (S >= 2) {
+                uint64_t ea[DM + 1], eb[DM + 1];
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
+                for (int e = 0; e <= DM; ++e) {
+                    ea[e] = pack2(ra[e], ra[e]);
+                    eb[e] = pack2(rb[e], rb[e]);
+                }
+#pragma unroll
+                for (int sp = 0; sp < S / 2; ++sp) {
+                    uint64_t aa = ea[0], bb = eb[0];
+#pragma unroll
+                    for (int l = 0; l < DM; ++l) {
+                        aa = ffma2(xp[sp][l], ea[1 + l], aa);
+                        bb = ffma2(xp[sp][l], eb[1 + l], bb);
+                    }
+                    float a0, a1, b0, b1;
+                    unpack2(aa, a0, a1);
+                    unpack2(bb, b0, b1);
+                    mc[2 * sp] = min3f(mc[2 * sp], a0, b0);
+                    mc[2 * sp + 1] = min3f(mc[2 * sp + 1], a1, b1);
+                }
+            }
+#pragma unroll
+            for (int s = (S / 2) * 2; s < S; ++s) {
                 float sa = ra[0], sb = rb[0];
 #pragma unroll
                 for (int l = 0; l < DM; ++l) {

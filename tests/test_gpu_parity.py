@@ -185,6 +185,25 @@ def test_tensor_core_adversarial_near_ties(ctx, B):
         assert stats.rechecks > 100
 
 
+@pytest.mark.parametrize("d", [1, 3, 5, 7, 9])
+def test_tensor_core_odd_dimensions(ctx, B, d):
+    """Dimensions between the compiled classes (zero-padded operand columns): cells of
+    near-tie, jittered and Gaussian samples against the oracle's exact search."""
+    rng = np.random.default_rng(100 + d)
+    N = 257 + 40 * d                      # a second, ragged operand tile
+    gA = rng.standard_normal((N, d))
+    gB = rng.standard_normal((N + 29, d)) * 0.8
+    X = np.concatenate([W.boundary_samples(gA, 1500, seed=d), W.boundary_samples(gA, 500, seed=d + 50, jitter=1e-6),
+                        rng.standard_normal((1003, d))])
+    Y = np.concatenate([W.boundary_samples(gB, 1500, seed=d + 7), rng.standard_normal((1503, d)) * 1.3])
+    counts, stats, ii, jj = ctx.counts_from_samples(_dev(gA), _dev(gB), _dev(X), _dev(Y),
+                                                    B.options(form=B.FORM_TC_RECHECK), want_cells=True)
+    np.testing.assert_array_equal(ii.cpu().numpy(), oracle.nearest(gA, X))
+    np.testing.assert_array_equal(jj.cpu().numpy(), oracle.nearest(gB, Y))
+    np.testing.assert_array_equal(counts.cpu().numpy(), oracle.counts_from_samples(gA, gB, X, Y))
+    assert stats.form_used == B.FORM_TC_RECHECK
+
+
 def test_tensor_core_timeout_is_reported(ctx, B):
     model = _model("ar8", M=600, n=2, N=4000)
     g = _dev(W.layer_grids(model, samples=12000, iters=2))
