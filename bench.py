@@ -75,7 +75,7 @@ def default_form(model, B):
 
 def plain_form(model, B):
     # the plain GPU comparator: exact FP64 brute force for d <= 2, FP32 brute force
-    # with FP64 recheck for d >= 4 (the path the learned and tensor forms are judged against)
+    # with FP64 recheck for d >= 4 (the path the learned and tensor forms are compared with)
     return B.FORM_PLAIN_F64 if model.d <= 2 else B.FORM_F32_RECHECK
 
 

@@ -5,7 +5,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call this file;
  * it exists so that the tests, the smoke check and the CPU-baseline leg of the
- * benchmark can judge the CUDA library.  It shares no source with the CUDA
+ * benchmark can check the CUDA library.  It shares no source with the CUDA
  * library: every function here is written from the paper (and, for the
  * sampler, from the published definitions it names) and nothing more.
  *

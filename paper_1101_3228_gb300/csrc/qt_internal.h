@@ -92,7 +92,7 @@ struct ForwardParams {
     const double* params_d;        // [n][param_count(d)]
     int32_t params_stride;
     // data
-    const double* g64;             // FP64 grids [sum N][d] (exactness judge)
+    const double* g64;             // FP64 grids [sum N][d] (the exact distances)
     const float* rec32;            // FP32 records [sum Npad][rec_floats]
     const double* rec64;           // FP64 records [sum Npad][rec64_doubles]
     const double* srcX;            // Source::kArrays: samples [M][d]
