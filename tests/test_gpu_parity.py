@@ -204,6 +204,21 @@ def test_tensor_core_odd_dimensions(ctx, B, d):
     assert stats.form_used == B.FORM_TC_RECHECK
 
 
+def test_tensor_core_fp64_samples_and_u32_counts(ctx, B):
+    """Tensor-core form on FP64 samples (the draw pass centres FP64 pairs) with uint32
+    counts, against the oracle's FP64 sampler and exact search."""
+    model = _model("ar8", M=3001, n=2, N=700)
+    g = W.layer_grids(model, samples=20000, iters=3)
+    counts, stats, _ = ctx.transitions(model, _dev(g), model.M, model.seed,
+                                       B.options(form=B.FORM_TC_RECHECK, prec=B.PREC_F64,
+                                                 counts_type=B.COUNTS_U32))
+    ref = oracle.transitions(model, g, model.M, model.seed, oracle.PREC_F64)
+    got = B.split_counts(model.N, counts.cpu().numpy().astype(np.int64))
+    for k in range(model.n):
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=f"layer {k}")
+    assert stats.form_used == B.FORM_TC_RECHECK and stats.device_status == 0
+
+
 def test_tensor_core_timeout_is_reported(ctx, B):
     model = _model("ar8", M=600, n=2, N=4000)
     g = _dev(W.layer_grids(model, samples=12000, iters=2))
