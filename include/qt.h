@@ -71,7 +71,8 @@ typedef int32_t qt_status;
 #define QT_EDEVICE 6         /* a kernel reported an internal inconsistency             */
 
 /* search forms (qt_options.form) */
-#define QT_FORM_AUTO 0        /* library picks the fastest certified form                */
+#define QT_FORM_AUTO 0        /* library picks the fastest certified form: TC_RECHECK for
+                                 3 <= d <= 10, F32_RECHECK otherwise                      */
 #define QT_FORM_PLAIN_F64 1   /* brute force, exact FP64 distances                       */
 #define QT_FORM_F32_RECHECK 2 /* FP32 brute-force screen, FP64 recheck of near ties      */
 #define QT_FORM_TC_RECHECK 3  /* tensor-core (tcgen05) screen, FP64 recheck              */
@@ -150,8 +151,8 @@ typedef struct {
     int32_t device_status;  /* qt_status reported by the kernels                      */
     double ms;              /* device time of the forward step, if measured, else 0   */
     int64_t diag[3];        /* tensor-core form: uncertified picks by cause (FP32 bound
-                               inside the two best chunks, tensor-core bound outside,
-                               index or FP16 range)                                    */
+                               inside the re-scored chunks, tensor-core bound outside
+                               them, index or FP16 range)                              */
 } qt_stats;
 
 /* Context: one per device.  device = CUDA ordinal.  Not thread safe; use one

@@ -12,27 +12,35 @@
 // DM <= 10.  The three cross products reproduce the FP32 score to about
 // 2^-21 relative (the tail x tail product is below 2^-22).
 //
-// A CTA is one persistent pipeline over its work items (layer k, 128 samples)
-// with three roles that meet only at mbarriers:
-//   producer warp    -- bulk copies of the grids' operand tiles (kept for the
-//                       whole layer when both grids fit, else streamed
-//                       through a ring) and the MMAs, one elected thread;
-//   two epilogue     -- warpgroup b reads accumulator b (tiles alternate
-//   warpgroups          between the two 256-column TMEM accumulators) with
-//                       tcgen05.ld and keeps, per sample, the two best
-//                       16-column chunks and the smallest other chunk minimum;
-//   four certifier   -- draw the samples of the next item (operand rows and
-//   warps               centred FP32 coordinates), then merge the two
-//                       warpgroups' chunk states of this item, certify,
-//                       recheck and count.
-// While the tensor cores work on item n, the certifiers draw item n + 1 and
-// certify item n - 1's results as they arrive.
+// Two passes per chunk of work items (layer k, 128 samples each):
+//   tc_draw_kernel    -- one CTA per item draws its 128 pairs, centres them on
+//                        both grids and writes the FP16 operand rows and the
+//                        centred FP32 samples (high occupancy, no pipeline);
+//   forward_tc_kernel -- one persistent CTA of 16 warps per SM, whose roles
+//                        meet only at mbarriers:
+//     two MMA warps        one per epilogue warpgroup; tile g of the CTA's
+//                          sequence goes to warpgroup g & 1, its two 128-point
+//                          halves to that warpgroup's two 128-column TMEM
+//                          accumulators (four in all);
+//     a loader warp        bulk copies of the grids' operand tiles, kept for
+//                          the whole layer when both grids fit, else streamed
+//                          through a ring;
+//     an operand loader    bulk copies of each item's drawn samples into one
+//                          of two item slots;
+//     two epilogue         read their accumulators with tcgen05.ld.red (the
+//     warpgroups           minimum of each 16-column chunk) and keep, per
+//                          sample, the two best chunks and the smallest other
+//                          chunk minimum;
+//     four certifier       merge the two warpgroups' chunk states, certify,
+//     warps                recheck and count.
+// While the tensor cores work on item n, the certifiers finish item n - 1.
 //
-// Exactness: the two best chunks are re-scored on the CUDA cores in FP32, and
-// the pick is certified against the exact FP64 distance with the FP32 bound
-// inside those chunks and the tensor-core bound outside them; uncertified
-// samples go to the exact window search (FP32 screen of the whole grid, exact
-// FP64 distances inside the certified window).
+// Exactness: the best chunk is re-scored on the CUDA cores in FP32 (and the
+// second one when the certificate needs it), and the pick is certified against
+// the exact FP64 distance with the FP32 bound inside the re-scored chunks and
+// the tensor-core bound outside them; uncertified samples go to the exact
+// window search (FP32 screen of the whole grid, exact FP64 distances inside
+// the certified window).
 #include <cuda_fp16.h>
 
 #include "qt_forward.cuh"
