@@ -139,12 +139,6 @@ struct Rec64 {
 
 // ------------------------------------------------------------------ sample access
 
-struct TileCtx {
-    const LayerDesc* L;      // shared-memory copy of the current layer descriptor
-    int k;
-    unsigned long long m0;   // first sample of the tile
-};
-
 // Exact sample (X or Y) of sample m as FP64 (regenerated for rechecks and dumps).
 template <int DM>
 __device__ __noinline__ void exact_sample(const ForwardParams& p, const float* spf, const double* spd, int k,
@@ -167,37 +161,6 @@ __device__ __noinline__ void exact_sample(const ForwardParams& p, const float* s
 #pragma unroll
         for (int l = 0; l < DM; ++l) z[l] = wantY ? Y[l] : X[l];
     }
-}
-
-// Warp-cooperative exact search for one lane's point z (broadcast from `src`):
-// lanes scan j = lane, lane+32, ... and the warp reduces (D64, j) lexicographically.
-template <int DM>
-__device__ __noinline__ int warp_exact_nn(const double (&z)[DM], int src_lane, const double* __restrict__ g,
-                                             int N, int d)
-{
-    double zz[DM];
-#pragma unroll
-    for (int l = 0; l < DM; ++l) zz[l] = __shfl_sync(0xFFFFFFFFu, z[l], src_lane);
-    const int lane = threadIdx.x & 31;
-    double best = __longlong_as_double(0x7FF0000000000000LL);  // +inf
-    int bi = 0x7FFFFFFF;
-    for (int j = lane; j < N; j += 32) {
-        const double dj = dist64<DM>(zz, g + (long long)j * d, d);
-        if (dj < best) {  // ascending j per lane: strict '<' keeps the lowest index
-            best = dj;
-            bi = j;
-        }
-    }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        const double ob = __shfl_xor_sync(0xFFFFFFFFu, best, off);
-        const int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, off);
-        if (ob < best || (ob == best && oi < bi)) {
-            best = ob;
-            bi = oi;
-        }
-    }
-    return bi;
 }
 
 // ------------------------------------------------------------------ FP32 screen
@@ -518,63 +481,10 @@ __device__ __forceinline__ bool screen_certified(int d, float A, float B1, float
     return (second - B1) > thr;
 }
 
-// Whole-warp FP32 re-screen of one lane's sample over a grid (records in global
-// memory); returns the certified cell or -1.
-template <int DM>
-__device__ __noinline__ int warp_screen_nn(const float (&xs)[DM], float A, int src, const float* __restrict__ recs,
-                                           int Npad, int d)
-{
-    constexpr int F = Rec32<DM>::kFloats;
-    float x[DM];
-#pragma unroll
-    for (int l = 0; l < DM; ++l) x[l] = __shfl_sync(0xFFFFFFFFu, xs[l], src);
-    const float Av = __shfl_sync(0xFFFFFFFFu, A, src);
-    const int lane = threadIdx.x & 31;
-    float b1 = __int_as_float(0x7F800000), b2 = __int_as_float(0x7F800000);
-    int i1 = 0x7FFFFFFF;
-    for (int j = lane; j < Npad; j += 32) {
-        const float* r = recs + j * F;
-        float sc = r[0];
-#pragma unroll
-        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], r[1 + l], sc);
-        if (sc < b1) {
-            b2 = b1;
-            b1 = sc;
-            i1 = j;
-        } else {
-            b2 = fminf(b2, sc);
-        }
-    }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        const float ob1 = __shfl_xor_sync(0xFFFFFFFFu, b1, off);
-        const float ob2 = __shfl_xor_sync(0xFFFFFFFFu, b2, off);
-        const int oi = __shfl_xor_sync(0xFFFFFFFFu, i1, off);
-        if (ob1 < b1 || (ob1 == b1 && oi < i1)) {
-            b2 = fminf(ob2, b1);
-            b1 = ob1;
-            i1 = oi;
-        } else {
-            b2 = fminf(b2, ob1);
-        }
-    }
-    const float* r = recs + i1 * F;
-    float n2 = 0.0f;
-#pragma unroll
-    for (int l = 0; l < DM; ++l) n2 = __fmaf_rn(r[1 + l], r[1 + l], n2);
-    return screen_certified(d, Av, b1, b2, __fsqrt_rn(n2)) ? i1 : -1;
-}
-
-
-// Exact cell of one lane's sample with almost no FP64 work.  The whole warp
-// screens the grid in FP32 (records in global memory) for the best score B1 at
-// index i1.  The exact FP64 argmin i* (and every point tied with it) has
-//   s_i* <= s_i1 + eta <= B1 + E(r1) + eta,  hence |g_i*| <= rho and
-//   s~_i* <= B1 + E(r1) + E(rho) + eta
-// (the bounds of screen_certified), so evaluating D64 only on the window
-// {j : s~_j <= B1 + E(r1) + E(rho) + eta} (with slack) and taking the lowest
-// index of the smallest D64 gives the contract's cell.  z: the lane's exact
-// FP64 sample, xs: -2 (sample - mu) in FP32, A: |sample - mu|.
+// Exact window search for one lane's sample (broadcast from lane `src`): the
+// warp screens the whole grid in FP32, then evaluates the exact FP64 distance
+// only on the records whose FP32 score lies inside the window the certificate's
+// bounds allow, and returns the lowest index among the smallest distances.
 template <int DM>
 __device__ __noinline__ int warp_window_nn(const float (&xs)[DM], float A, const double (&z)[DM], int src,
                                            const float* __restrict__ recs, int Npad, const double* __restrict__ g64,
