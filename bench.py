@@ -417,7 +417,8 @@ def main():
                            "uncertified_by_cause": diag if form == B.FORM_TC_RECHECK else None,
                            "router": router_info,
                            "candidates_per_search": (cand / (2 * units)) if router else None},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (tc_launches_per_step(model) if form == B.FORM_TC_RECHECK else 2) * args.steps,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (tc_launches_per_step(model) if form == B.FORM_TC_RECHECK
+                                 else 3 if form == B.FORM_ROUTER_CERT else 2) * args.steps,
                 "clocks": clocks, "plain": plain}
         print(json.dumps(line), flush=True)
     ctx.close()
