@@ -91,6 +91,8 @@ typedef int32_t qt_status;
 #define QT_FLAG_NO_TUNE 2u    /* skip the autotuner, use the built-in tile choice            */
 #define QT_FLAG_SMEM_HIST 4u  /* force the shared-memory privatised histogram                */
 #define QT_FLAG_GLOBAL_HIST 8u /* force direct L2 atomics for the counts                     */
+#define QT_FLAG_FUSED_BACKWARD 16u /* qt_price: layer pairs in reverse order, each pair's counts
+                                    folded into V at once (one pair's counts in memory)       */
 
 /* grid-building methods (qt_build_grids) */
 #define QT_GRID_LLOYD1D 1     /* d = 1: stationary quantizer of N(0,1) (Newton on Lloyd's map) */

@@ -20,7 +20,7 @@ QT_OK, QT_EINVAL, QT_ENOMEM, QT_ECUDA, QT_ETIMEOUT, QT_EUNSUPPORTED, QT_EDEVICE 
 FORM_AUTO, FORM_PLAIN_F64, FORM_F32_RECHECK, FORM_TC_RECHECK, FORM_ROUTER_CERT = range(5)
 PREC_F64, PREC_F32 = 0, 1
 COUNTS_I64, COUNTS_U32 = 0, 1
-FLAG_NO_GRAPH, FLAG_NO_TUNE, FLAG_SMEM_HIST, FLAG_GLOBAL_HIST = 1, 2, 4, 8
+FLAG_NO_GRAPH, FLAG_NO_TUNE, FLAG_SMEM_HIST, FLAG_GLOBAL_HIST, FLAG_FUSED_BACKWARD = 1, 2, 4, 8, 16
 GRID_LLOYD1D, GRID_PRODUCT, GRID_KMEANS = 1, 2, 3
 
 FORM_NAMES = {FORM_AUTO: "auto", FORM_PLAIN_F64: "plain_f64", FORM_F32_RECHECK: "f32_recheck",

@@ -319,10 +319,36 @@ struct FwdIO {
     int32_t* cellsB;
 };
 
+qt_status make_plan_full(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, long long M,
+                         const qt_options* o, bool from_arrays, Plan& P);
+
+// The plan of the whole model, or of layer pair `only_layer` alone: the other
+// layers keep their descriptors (so that every kernel still finds layer k by
+// its global index, which also keys the sampler's counters) but get no work
+// items, and layer k's counts start at offset 0 of the counts buffer.
+qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, long long M, const qt_options* o,
+                    bool from_arrays, Plan& P, int only_layer = -1)
+{
+    qt_status s = make_plan_full(ctx, d, n, Ns, mus, M, o, from_arrays, P);
+    if (s || only_layer < 0) return s;
+    if (only_layer >= n) return fail(ctx, QT_EINVAL, "layer %d of %d", only_layer, n);
+    const int items = P.layers[only_layer].items;
+    for (int k = 0; k < n; ++k) {
+        P.layers[k].item_begin = k <= only_layer ? 0 : items;
+        if (k != only_layer) P.layers[k].items = 0;
+    }
+    P.layers[only_layer].coff = 0;
+    P.total_items = items;
+    P.count_entries = (long long)P.layers[only_layer].NA * P.layers[only_layer].NB;
+    if (P.form == kTcRecheck)
+        P.tc_chunk_items = std::max<long long>(1, std::min<long long>(P.total_items, (2ll << 30) / (long long)P.tc_item_bytes));
+    return QT_OK;
+}
+
 // Pick form, dimension class, tile and shared memory for a problem described
 // by grid sizes Ns (n+1 entries) and centres mus ((n+1) x d).
-qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, long long M, const qt_options* o,
-                    bool from_arrays, Plan& P)
+qt_status make_plan_full(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, long long M,
+                         const qt_options* o, bool from_arrays, Plan& P)
 {
     P.d = d;
     P.n = n;
@@ -857,10 +883,10 @@ TuneKey tune_key(const Plan& P, int prec, const int64_t* Ns, int n)
 // Shared body of qt_transitions and qt_counts_from_samples.
 qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, const double* params_d_host,
                          long long M, unsigned long long seed, const qt_options* o, int source, const FwdIO& io,
-                         qt_stats* stats, cudaStream_t st)
+                         qt_stats* stats, cudaStream_t st, int only_layer = -1)
 {
     Plan P;
-    qt_status s = make_plan(ctx, d, n, Ns, mus, M, o, source == kArrays, P);
+    qt_status s = make_plan(ctx, d, n, Ns, mus, M, o, source == kArrays, P, only_layer);
     if (s) return s;
     const bool capturing = stream_is_capturing(st);
     if (P.form != kTcRecheck && P.form != kRouterCert && o->tile_samples_per_thread <= 0 && !(o->flags & QT_FLAG_NO_TUNE) && !capturing &&
@@ -872,14 +898,15 @@ qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
         qt_options to = *o;
         to.tile_samples_per_thread = ctx->tune[key];
         Plan P2;
-        if ((s = make_plan(ctx, d, n, Ns, mus, M, &to, source == kArrays, P2))) return s;
+        if ((s = make_plan(ctx, d, n, Ns, mus, M, &to, source == kArrays, P2, only_layer))) return s;
         P = P2;
     }
     ctx->last_form = P.form == kPlainF64    ? QT_FORM_PLAIN_F64
                      : P.form == kTcRecheck ? QT_FORM_TC_RECHECK
                      : P.form == kRouterCert ? QT_FORM_ROUTER_CERT
                                              : QT_FORM_F32_RECHECK;
-    const bool use_graph = !(o->flags & QT_FLAG_NO_GRAPH) && !capturing;
+    // one layer at a time (fused backward) launches directly: each layer would be a new graph
+    const bool use_graph = !(o->flags & QT_FLAG_NO_GRAPH) && !capturing && only_layer < 0;
     if ((s = run_plan(ctx, P, io, M, seed, o, source, params_d_host, st, use_graph, ""))) return s;
     if (stats) return read_status(ctx, st, stats, (long long)n * M, 2ll * n * M);
     return QT_OK;
@@ -902,9 +929,25 @@ void pack_params(const qt_model* m, int k, int pstride, double* out)
 
 }  // namespace
 
+namespace {
+qt_status transitions_impl(qt_ctx* ctx, const qt_model* model, const double* grids, int64_t M, uint64_t seed,
+                           const qt_options* opts, void* counts, const qt_dump* dump, qt_stats* stats, void* stream,
+                           int only_layer);
+}
+
 extern "C" qt_status qt_transitions(qt_ctx* ctx, const qt_model* model, const double* grids, int64_t M, uint64_t seed,
                                     const qt_options* opts, void* counts, const qt_dump* dump, qt_stats* stats,
                                     void* stream)
+{
+    return transitions_impl(ctx, model, grids, M, seed, opts, counts, dump, stats, stream, -1);
+}
+
+namespace {
+// qt_transitions for all layers, or for layer pair `only_layer` alone (its
+// counts at the start of `counts`).
+qt_status transitions_impl(qt_ctx* ctx, const qt_model* model, const double* grids, int64_t M, uint64_t seed,
+                           const qt_options* opts, void* counts, const qt_dump* dump, qt_stats* stats, void* stream,
+                           int only_layer)
 {
     if (!ctx) return QT_EINVAL;
     qt_status s = validate_model(ctx, model);
@@ -930,8 +973,9 @@ extern "C" qt_status qt_transitions(qt_ctx* ctx, const qt_model* model, const do
     io.counts = counts;
     io.dump = (dump && dump->count > 0) ? dump : nullptr;
     return forward_common(ctx, d, n, model->N, model->m, params.data(), M, seed, &o, kSampler, io, stats,
-                          (cudaStream_t)stream);
+                          (cudaStream_t)stream, only_layer);
 }
+}  // namespace
 
 extern "C" qt_status qt_counts_from_samples(qt_ctx* ctx, int32_t d, const double* gA, int64_t NA, const double* gB,
                                             int64_t NB, const double* X, const double* Y, int64_t M,
@@ -1048,6 +1092,12 @@ extern "C" qt_status qt_price(qt_ctx* ctx, const qt_model* model, const double* 
     for (int k = 0; k <= n; ++k) pts += model->N[k];
     for (int k = 0; k < n; ++k) ent += model->N[k] * model->N[k + 1];
     const size_t csize = o.counts_type == QT_COUNTS_U32 ? 4 : 8;
+    const bool fused = (o.flags & QT_FLAG_FUSED_BACKWARD) != 0;
+    if (fused) {
+        // one layer's counts at a time
+        ent = 0;
+        for (int k = 0; k < n; ++k) ent = std::max<long long>(ent, model->N[k] * model->N[k + 1]);
+    }
     void *dcounts, *dV, *dout;
     if ((s = dev_get(ctx, "price_counts", csize * (size_t)ent, &dcounts))) return s;
     if ((s = dev_get(ctx, "price_V", sizeof(double) * (size_t)pts, &dV))) return s;
@@ -1066,8 +1116,29 @@ extern "C" qt_status qt_price(qt_ctx* ctx, const qt_model* model, const double* 
         QT_CUDA(cudaMemcpyAsync(p, phi, sizeof(double) * (size_t)pts, cudaMemcpyHostToDevice, st));
         dphi = (const double*)p;
     }
-    if ((s = qt_transitions(ctx, model, dgrids, M, seed, &o, dcounts, nullptr, nullptr, stream))) return s;
-    if ((s = qt_backward(ctx, n, model->N, dcounts, o.counts_type, dphi, (double*)dV, stream))) return s;
+    if (!fused) {
+        if ((s = qt_transitions(ctx, model, dgrids, M, seed, &o, dcounts, nullptr, nullptr, stream))) return s;
+        if ((s = qt_backward(ctx, n, model->N, dcounts, o.counts_type, dphi, (double*)dV, stream))) return s;
+    } else {
+        // layers in reverse order: the counts of pair (k, k + 1), then V_k from
+        // them and V_{k+1} at once (the same kernels and arithmetic as the
+        // unfused path, so the same bits); the counts left at the end are
+        // layer 0's, which the root value reads
+        std::vector<long long> goff(n + 2, 0);
+        for (int k = 0; k <= n; ++k) goff[k + 1] = goff[k] + model->N[k];
+        double* V = (double*)dV;
+        QT_CUDA(cudaMemcpyAsync(V + goff[n], dphi + goff[n], sizeof(double) * model->N[n], cudaMemcpyDeviceToDevice,
+                                st));
+        for (int k = n - 1; k >= 0; --k) {
+            if ((s = transitions_impl(ctx, model, dgrids, M, seed, &o, dcounts, nullptr, nullptr, stream, k)))
+                return s;
+            const long long threads = model->N[k] * 32;
+            backward_layer_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+                dcounts, o.counts_type == QT_COUNTS_U32, 0, (int)model->N[k], (int)model->N[k + 1], dphi + goff[k],
+                V + goff[k + 1], V + goff[k]);
+            QT_CUDA(cudaGetLastError());
+        }
+    }
     root_price_kernel<<<1, 32, 0, st>>>(dcounts, o.counts_type == QT_COUNTS_U32, (int)model->N[0], (int)model->N[1],
                                         (const double*)dV, (double*)dout);
     QT_CUDA(cudaGetLastError());

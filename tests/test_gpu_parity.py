@@ -358,6 +358,25 @@ def test_price_matches_oracle_with_host_buffers(ctx, B):
     assert abs(p_dev - ref) <= 1e-12 * abs(ref)
 
 
+@pytest.mark.parametrize("name,N,form,flags", [("ou2", 64, "f32", 0), ("ou2", 500, "f32", 0),
+                                                ("basket4", 0, "tc", 0), ("ou2", 300, "f32", "graph")])
+def test_fused_backward_price_is_bit_identical(ctx, B, name, N, form, flags):
+    """Layer pairs in reverse order, each pair's counts folded into V at once (one pair's
+    counts in memory): the same price bits as the unfused path, and the oracle's within 1e-12."""
+    model = _model(name, M=20011, n=4, N=N) if N else _model(name, M=20011, n=4)
+    g = W.layer_grids(model, samples=20000, iters=3) if model.grid_kind == "kmeans" else W.layer_grids(model)
+    phi = W.payoff_values(model, g)
+    f = B.FORM_F32_RECHECK if form == "f32" else B.FORM_TC_RECHECK
+    base = 0 if flags == "graph" else B.FLAG_NO_GRAPH
+    p0, _ = ctx.price(model, _dev(g), model.M, model.seed, _dev(phi), B.options(form=f, flags=base))
+    p1, st = ctx.price(model, _dev(g), model.M, model.seed, _dev(phi),
+                       B.options(form=f, flags=base | B.FLAG_FUSED_BACKWARD))
+    assert st.device_status == 0
+    assert p1 == p0
+    ref = oracle.price(model.N, oracle.transitions(model, g, model.M, model.seed, oracle.PREC_F32), phi)
+    assert abs(p1 - ref) <= 1e-12 * abs(ref)
+
+
 def test_build_grids_lloyd1d_and_product(ctx, B):
     model = W.bs1d()
     g = ctx.build_grids(model, B.GRID_LLOYD1D).cpu().numpy()
