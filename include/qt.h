@@ -129,7 +129,10 @@ typedef struct {
                               negative = give up at once (tests of the timeout path)       */
     const void* router;    /* qt_router* for QT_FORM_ROUTER_CERT, else NULL                */
     int32_t tile_samples_per_thread; /* 0 = autotuned                                       */
-    int32_t reserved[3];
+    int32_t tc_chunk_items; /* tensor-core form: most work items (128 samples each) drawn per
+                              draw pass and screened per forward pass; 0 = as many as 2 GiB
+                              of drawn samples hold                                        */
+    int32_t reserved[2];
 } qt_options;
 
 /* Optional per-sample record: sample t of layer k is m = t * stride, t < count.
@@ -295,8 +298,11 @@ QT_API qt_status qt_router_loss_grad(qt_ctx* ctx, const qt_router* router, const
  * without a context: the scratch (status and queue words, descriptors, a copy
  * of both grids, their screened records) is a fixed array inside the library,
  * one per device, kept until the process exits.  It calls no allocation
- * routine.  The first call on a device looks up the array's device address;
- * make that first call before any stream capture.  Every call reuses the same
+ * routine.  The first call on a device looks up the array's device address and
+ * two device attributes and keeps them for the life of the process; make that
+ * first call before any stream capture, and do not call this entry point on a
+ * device after cudaDeviceReset (the kept address would be stale).  Every call
+ * reuses the same
  * array, so calls that overlap on the GPU (two streams, two host threads)
  * race: serialise them.  The call synchronises `stream` and returns the
  * kernels' status.

@@ -43,7 +43,7 @@ class QtModel(ctypes.Structure):
 
 class QtOptions(ctypes.Structure):
     _fields_ = [("form", i32), ("sample_prec", i32), ("counts_type", i32), ("flags", u32),
-                ("spin_budget", i64), ("router", P), ("tile_samples_per_thread", i32), ("reserved", i32 * 3)]
+                ("spin_budget", i64), ("router", P), ("tile_samples_per_thread", i32), ("tc_chunk_items", i32), ("reserved", i32 * 2)]
 
 
 class QtDump(ctypes.Structure):
@@ -157,12 +157,13 @@ class HostModel:
 
 
 def options(form=FORM_AUTO, prec=PREC_F32, counts_type=COUNTS_I64, flags=0, spin_budget=0, router=None,
-            samples_per_thread=0) -> QtOptions:
+            samples_per_thread=0, tc_chunk_items=0) -> QtOptions:
     o = QtOptions()
     o.form, o.sample_prec, o.counts_type, o.flags = form, prec, counts_type, flags
     o.spin_budget = spin_budget
     o.router = router
     o.tile_samples_per_thread = samples_per_thread
+    o.tc_chunk_items = tc_chunk_items
     return o
 
 

@@ -22,6 +22,7 @@ namespace qt {
 __global__ void prep_records_kernel(const double*, GridInfo*, int, int, int, int, long long, float*, double*);
 __global__ void backward_layer_kernel(const void*, int, long long, int, int, const double*, const double*, double*);
 __global__ void root_price_kernel(const void*, int, int, int, const double*, double*);
+__global__ void fold_status_kernel(const DevStatus*, DevStatus*);
 __global__ void kmeans_draw_kernel(int, unsigned long long, long long, float*);
 __global__ void kmeans_assign_kernel(int, long long, const float*, int, const float*, unsigned long long*,
                                      unsigned long long*, int);
@@ -125,6 +126,16 @@ bool injected_alloc_failure()
 {
     const char* f = getenv("QT_FAULT");
     return f && strcmp(f, "alloc") == 0;
+}
+
+// QT_FAULT=timeout_layer:K gives the launch that runs layer pair K alone (the
+// fused price mode) a negative wait budget, so that its first bounded wait
+// gives up as if the copy never landed: a timeout in one layer only.
+int injected_timeout_layer()
+{
+    const char* f = getenv("QT_FAULT");
+    if (!f || strncmp(f, "timeout_layer:", 14) != 0) return -1;
+    return atoi(f + 14);
 }
 
 qt_status dev_get(qt_ctx* ctx, const char* name, size_t bytes, void** out)
@@ -322,6 +333,15 @@ struct FwdIO {
 qt_status make_plan_full(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, long long M,
                          const qt_options* o, bool from_arrays, Plan& P);
 
+// Work items per draw/forward pass of the tensor-core form: as many as 2 GiB of
+// drawn samples hold, or fewer when the caller caps it.
+long long tc_chunk(const Plan& P, const qt_options* o)
+{
+    long long c = std::min<long long>(P.total_items, (2ll << 30) / (long long)P.tc_item_bytes);
+    if (o->tc_chunk_items > 0) c = std::min<long long>(c, o->tc_chunk_items);
+    return std::max<long long>(1, c);
+}
+
 // The plan of the whole model, or of layer pair `only_layer` alone: the other
 // layers keep their descriptors (so that every kernel still finds layer k by
 // its global index, which also keys the sampler's counters) but get no work
@@ -340,8 +360,7 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
     P.layers[only_layer].coff = 0;
     P.total_items = items;
     P.count_entries = (long long)P.layers[only_layer].NA * P.layers[only_layer].NB;
-    if (P.form == kTcRecheck)
-        P.tc_chunk_items = std::max<long long>(1, std::min<long long>(P.total_items, (2ll << 30) / (long long)P.tc_item_bytes));
+    if (P.form == kTcRecheck) P.tc_chunk_items = tc_chunk(P, o);
     return QT_OK;
 }
 
@@ -480,7 +499,7 @@ qt_status make_plan_full(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
             coff += (long long)L.NA * L.NB;
         }
         P.total_items = item;
-        P.tc_chunk_items = std::max<long long>(1, std::min<long long>(P.total_items, (2ll << 30) / (long long)P.tc_item_bytes));
+        P.tc_chunk_items = tc_chunk(P, o);
         P.count_entries = coff;
         return QT_OK;
     }
@@ -885,6 +904,12 @@ qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
                          long long M, unsigned long long seed, const qt_options* o, int source, const FwdIO& io,
                          qt_stats* stats, cudaStream_t st, int only_layer = -1)
 {
+    qt_options oi;
+    if (only_layer >= 0 && only_layer == injected_timeout_layer()) {
+        oi = *o;
+        oi.spin_budget = -1;
+        o = &oi;
+    }
     Plan P;
     qt_status s = make_plan(ctx, d, n, Ns, mus, M, o, source == kArrays, P, only_layer);
     if (s) return s;
@@ -1127,17 +1152,26 @@ extern "C" qt_status qt_price(qt_ctx* ctx, const qt_model* model, const double* 
         std::vector<long long> goff(n + 2, 0);
         for (int k = 0; k <= n; ++k) goff[k + 1] = goff[k] + model->N[k];
         double* V = (double*)dV;
+        // each layer's launch clears its own status block: fold every one into
+        // an accumulator, so that an error in any layer reaches the caller
+        void* dacc;
+        if ((s = dev_get(ctx, "price_status", sizeof(DevStatus), &dacc))) return s;
+        QT_CUDA(cudaMemsetAsync(dacc, 0, sizeof(DevStatus), st));
         QT_CUDA(cudaMemcpyAsync(V + goff[n], dphi + goff[n], sizeof(double) * model->N[n], cudaMemcpyDeviceToDevice,
                                 st));
         for (int k = n - 1; k >= 0; --k) {
             if ((s = transitions_impl(ctx, model, dgrids, M, seed, &o, dcounts, nullptr, nullptr, stream, k)))
                 return s;
+            fold_status_kernel<<<1, 1, 0, st>>>((const DevStatus*)ctx->status_buf, (DevStatus*)dacc);
+            QT_CUDA(cudaGetLastError());
             const long long threads = model->N[k] * 32;
             backward_layer_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
                 dcounts, o.counts_type == QT_COUNTS_U32, 0, (int)model->N[k], (int)model->N[k + 1], dphi + goff[k],
                 V + goff[k + 1], V + goff[k]);
             QT_CUDA(cudaGetLastError());
         }
+        // the status the caller reads is the accumulated one
+        QT_CUDA(cudaMemcpyAsync(ctx->status_buf, dacc, sizeof(DevStatus), cudaMemcpyDeviceToDevice, st));
     }
     root_price_kernel<<<1, 32, 0, st>>>(dcounts, o.counts_type == QT_COUNTS_U32, (int)model->N[0], (int)model->N[1],
                                         (const double*)dV, (double*)dout);

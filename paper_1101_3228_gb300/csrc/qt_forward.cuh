@@ -20,11 +20,14 @@
 //  * FP32 screen: scores s_j = |c_j - mu|^2 - 2 (x - mu).(c_j - mu) with FMA
 //    chains on centred FP32 copies; the running minimum is tracked per chunk of
 //    kChunk candidates (one 3-input min per candidate pair), the best chunk is
-//    re-scored at the end for the index and the second-best score.  A sample is
-//    certified when  s_2nd - s_best > (d+2) (R + |x^|)^2 2^-22,  twice a bound
-//    on |s~_j - s_j| plus the FP64 rounding of the exact distance (R = max norm
-//    of the centred grid, x^ the centred sample).  Uncertified samples are
-//    re-evaluated exactly in FP64 by the whole warp.
+//    re-scored at the end for the index and the second-best score.  With
+//    E(r) = (d+2) 2^-24 (r^2 + 2|x^| r) the bound on |s~_j - s_j| for a grid
+//    point at distance r from the centre, a sample is certified when
+//    s_2nd - s_best > E(rho) + E(r_best) + eta, rho the largest radius at which
+//    a point can still beat the best (see screen_certified for the test as
+//    evaluated, with its slack factors; x^ is the centred sample and eta covers
+//    the FP64 rounding of the exact distance).  Uncertified samples go to the
+//    exact window search of the whole warp (warp_window_nn).
 #pragma once
 #include <cstdint>
 #include <cfloat>

@@ -111,6 +111,22 @@ __global__ void backward_layer_kernel(const void* __restrict__ counts, int u32, 
     }
 }
 
+// Status of one launch folded into an accumulator (the fused price mode runs
+// one launch per layer pair, each clearing its own status block): the first
+// error code and site are kept, the counters are summed.  One thread.
+__global__ void fold_status_kernel(const DevStatus* __restrict__ src, DevStatus* acc)
+{
+    if (acc->code == 0 && src->code != 0) {
+        acc->code = src->code;
+        acc->where = src->where;
+    }
+    acc->rechecks += src->rechecks;
+    acc->candidates += src->candidates;
+    acc->done_items += src->done_items;
+    acc->spare[0] = src->spare[0];
+    for (int q = 1; q < 4; ++q) acc->spare[q] += src->spare[q];
+}
+
 // Root value: sum_i (p^0_i / M) V_0(i), one warp, same fixed order as above.
 __global__ void root_price_kernel(const void* __restrict__ counts, int u32, int N0, int N1,
                                   const double* __restrict__ V0, double* out)

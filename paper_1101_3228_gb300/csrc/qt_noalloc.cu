@@ -51,21 +51,36 @@ static_assert(sizeof(DevStatus) <= 256 && sizeof(LayerDesc) <= 256 && 2 * sizeof
 static __device__ __align__(256) unsigned char qt_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void* g_scratch[kMaxDevices] = {};
 
-// Once per device, with that device current: the device address of the array.
-cudaError_t scratch_address(int dev, unsigned char** out)
+// What a call needs to know about its device, looked up once per device.
+struct DeviceSetup {
+    void* scratch = nullptr;   // device address of qt_noalloc_scratch on this device
+    int num_sms = 0;           // multiprocessors (grid size of the persistent kernel)
+    int smem_optin = 0;        // opt-in shared memory per block (the resident-grid budget)
+};
+std::mutex g_setup_mutex;
+DeviceSetup g_setup[kMaxDevices];
+
+// Once per device, with that device current: the device address of the array
+// and the two device attributes the plan needs (cudaDeviceGetAttribute, so that
+// later calls query nothing).
+cudaError_t device_setup(int dev, DeviceSetup* out)
 {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, qt_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch[dev] = p;
+    DeviceSetup& s = g_setup[dev];
+    if (!s.scratch) {
+        DeviceSetup n;
+        cudaError_t e = cudaDeviceGetAttribute(&n.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&n.scratch, qt_noalloc_scratch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        s = n;
     }
-    *out = static_cast<unsigned char*>(g_scratch[dev]);
+    *out = s;
     return cudaSuccess;
 }
 
@@ -96,10 +111,9 @@ extern "C" qt_status qt_counts_from_samples_noalloc(int32_t d, const double* gA,
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return QT_ECUDA;
-    cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return QT_ECUDA;
-    unsigned char* base = nullptr;
-    if (scratch_address(dev, &base) != cudaSuccess) return QT_ECUDA;
+    DeviceSetup ds;
+    if (device_setup(dev, &ds) != cudaSuccess) return QT_ECUDA;
+    unsigned char* base = static_cast<unsigned char*>(ds.scratch);
 
     // plan: FP32 screen with FP64 recheck, both grids resident in shared memory
     const int dm = dim_class(d);
@@ -108,7 +122,7 @@ extern "C" qt_status qt_counts_from_samples_noalloc(int32_t d, const double* gA,
     const int block = 256;
     const long long NApad = up(NA, kChunk), NBpad = up(NB, kChunk);
     const size_t grid_bytes = (size_t)up((NApad + NBpad) * rec_floats * 4, 128);
-    const size_t budget = prop.sharedMemPerBlockOptin > 24 * 1024 ? prop.sharedMemPerBlockOptin - 24 * 1024 : 0;
+    const size_t budget = ds.smem_optin > 24 * 1024 ? (size_t)ds.smem_optin - 24 * 1024 : 0;
     if (grid_bytes > budget || !forward_variant_exists(kF32Recheck, dm, S, false)) return QT_EINVAL;
 
     DevStatus* dstatus = reinterpret_cast<DevStatus*>(base + kOffStatus);
@@ -188,7 +202,7 @@ extern "C" qt_status qt_counts_from_samples_noalloc(int32_t d, const double* gA,
     fp.cellsB = jj;
     fp.status = dstatus;
     int bps = 0;
-    if (forward_launch(kF32Recheck, dm, S, false, fp, block, (int)grid_bytes, prop.multiProcessorCount, &bps, st) !=
+    if (forward_launch(kF32Recheck, dm, S, false, fp, block, (int)grid_bytes, ds.num_sms, &bps, st) !=
         cudaSuccess)
         return QT_ECUDA;
 

@@ -377,6 +377,27 @@ def test_fused_backward_price_is_bit_identical(ctx, B, name, N, form, flags):
     assert abs(p1 - ref) <= 1e-12 * abs(ref)
 
 
+@pytest.mark.parametrize("layer", [3, 1])
+def test_fused_backward_reports_a_timeout_in_one_layer(ctx, B, layer):
+    """A bounded wait that gives up in one layer pair k > 0 only (host-side injection:
+    that layer's launch alone gets a negative wait budget) must reach the caller of the
+    fused price, although the layers after it (k - 1 .. 0) run clean launches."""
+    model = _model("ou2", M=20011, n=4, N=64)
+    g = _dev(_grids(model))
+    phi = _dev(W.payoff_values(model, _grids(model)))
+    os.environ["QT_FAULT"] = f"timeout_layer:{layer}"
+    try:
+        with pytest.raises(B.QtError) as e:
+            ctx.price(model, g, model.M, model.seed, phi, B.options(form=B.FORM_F32_RECHECK,
+                                                                   flags=B.FLAG_FUSED_BACKWARD))
+        assert e.value.status == B.QT_ETIMEOUT
+    finally:
+        del os.environ["QT_FAULT"]
+    p, st = ctx.price(model, g, model.M, model.seed, phi, B.options(form=B.FORM_F32_RECHECK,
+                                                                   flags=B.FLAG_FUSED_BACKWARD))
+    assert st.device_status == 0
+
+
 def test_build_grids_lloyd1d_and_product(ctx, B):
     model = W.bs1d()
     g = ctx.build_grids(model, B.GRID_LLOYD1D).cpu().numpy()

@@ -96,3 +96,18 @@ def test_router_rejects_other_grids(ctx, B, ar8_case):
     with pytest.raises(B.QtError) as e:
         ctx.transitions(model, other, model.M, model.seed, B.options(form=B.FORM_ROUTER_CERT, router=trained.handle))
     assert e.value.status == B.QT_EINVAL
+
+
+def test_router_fused_backward_price(ctx, B, ar8_case):
+    """The fused reverse-order price with the router form: every layer pair in its own
+    launch (the router finds its layer by the global index), the same price bits as the
+    unfused path and the oracle's price within 1e-12."""
+    model, g, gd, trained, _ = ar8_case
+    phi = W.payoff_values(model, g)
+    o = dict(form=B.FORM_ROUTER_CERT, router=trained.handle)
+    p0, _ = ctx.price(model, gd, model.M, model.seed, _dev(phi), B.options(**o))
+    p1, st = ctx.price(model, gd, model.M, model.seed, _dev(phi), B.options(flags=B.FLAG_FUSED_BACKWARD, **o))
+    assert st.device_status == 0 and st.form_used == B.FORM_ROUTER_CERT
+    assert p1 == p0
+    ref = oracle.price(model.N, oracle.transitions(model, g, model.M, model.seed, oracle.PREC_F32), phi)
+    assert abs(p1 - ref) <= 1e-12 * abs(ref)

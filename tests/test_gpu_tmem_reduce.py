@@ -3,7 +3,6 @@ tensor-memory loads (tcgen05.ld.red ... .min.f32).  This test pins what that
 instruction returns on this GPU: the exact per-thread minimum (and maximum) of the
 loaded columns, with the loaded values intact, for known contents."""
 import os
-import shutil
 import subprocess
 import tempfile
 
@@ -14,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 @pytest.mark.gpu
 def test_tmem_load_reduction_is_the_exact_min():
-    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    from paper_1101_3228_gb300.build import _nvcc
+    nvcc = _nvcc()            # NVCC, PATH, then the toolkit's standard location
     with tempfile.TemporaryDirectory() as tmp:
         exe = os.path.join(tmp, "tmem_ld_red")
         subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2",

@@ -8,6 +8,7 @@ Citations are to Pages & Wilbertz, arXiv:1101.3228.
 import ctypes
 import math
 import os
+import shutil
 
 import numpy as np
 import pytest
@@ -17,7 +18,25 @@ from scipy.spatial import cKDTree
 import oracle
 import qt_workloads as W
 
-CURAND = "/usr/local/cuda/lib64/libcurand.so"
+def _find_curand():
+    """cuRAND's shared library: the loader's search path first, then the toolkit under CUDA_HOME."""
+    import ctypes.util
+    import glob
+    name = ctypes.util.find_library("curand")
+    if name:
+        return name
+    nvcc = shutil.which("nvcc")
+    homes = [os.environ.get("CUDA_HOME"), os.environ.get("CUDA_PATH"),
+             os.path.dirname(os.path.dirname(nvcc)) if nvcc else None]
+    for h in homes:
+        if h:
+            hits = sorted(glob.glob(os.path.join(h, "lib*", "libcurand.so*")))
+            if hits:
+                return hits[0]
+    return None
+
+
+CURAND = _find_curand()
 
 
 # --------------------------------------------------------------------------- Philox (Sec. 3.1 generator)
@@ -36,7 +55,7 @@ def _curand_host_blocks(seed: int, offset_words: int, nblocks: int) -> np.ndarra
     return out.reshape(nblocks, 4)
 
 
-@pytest.mark.skipif(not os.path.exists(CURAND), reason="libcurand not installed")
+@pytest.mark.skipif(CURAND is None, reason="libcurand not installed")
 @pytest.mark.parametrize("seed,offset_blocks", [
     (0, 0), (0x0123456789ABCDEF, 0), (0xDEADBEEF12345678, (3 << 48) + 65536 * 9 + 11),
     (0x0000C0FFEE000002, 65536 * 77 + 5)])

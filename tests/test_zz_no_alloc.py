@@ -10,10 +10,10 @@ sizes, must each equal qt_counts_from_samples on the same inputs (counts and
 cells bit for bit, the tolerance of every count test), which also shows that
 the shared scratch keeps nothing from the previous call.
 """
-import ctypes
-
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -66,3 +66,36 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(gpu_lib):
     gA, gB, X, Y = _case(rng, 2, 3000, 2000, 100)     # NA + NB > QT_NOALLOC_MAX_POINTS
     st, _, _, _ = _noalloc(lib, gA, gB, X, Y)
     assert st == B.QT_EINVAL
+
+
+def test_noalloc_rejects_records_beyond_shared_memory(gpu_lib):
+    """d = 16 with 4096 points fits the scratch array but not one CTA's shared memory
+    (about 330 KB of screened records): rejected before any work is enqueued."""
+    from paper_1101_3228_gb300 import binding as B
+    lib = B.load()
+    rng = np.random.default_rng(5)
+    gA, gB, X, Y = _case(rng, 16, 2048, 2048, 64)
+    st, _, _, _ = _noalloc(lib, gA, gB, X, Y)
+    assert st == B.QT_EINVAL
+
+
+@pytest.mark.parametrize("d,NA,NB,M", [(1, 100, 37, 5003), (3, 300, 211, 2011), (16, 200, 150, 1999)])
+def test_noalloc_matches_the_oracle(gpu_lib, d, NA, NB, M):
+    """Small cases at the dimension bounds against the FP64 oracle's brute-force
+    cells and counts, with near-tie samples on the grids' bisectors."""
+    import qt_workloads as W
+    from paper_1101_3228_gb300 import binding as B
+    lib = B.load()
+    rng = np.random.default_rng(40 + d)
+    ga = rng.standard_normal((NA, d))
+    gb = rng.standard_normal((NB, d)) * 1.2
+    half = M // 2
+    x = np.concatenate([W.boundary_samples(ga, half, seed=d), rng.standard_normal((M - half, d))])
+    y = np.concatenate([rng.standard_normal((M - half, d)), W.boundary_samples(gb, half, seed=d + 1)])
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (ga, gb, x, y)]
+    for _ in range(2):
+        st, counts, ii, jj = _noalloc(lib, *dev)
+        assert st == B.QT_OK
+        np.testing.assert_array_equal(ii.cpu().numpy(), oracle.nearest(ga, x))
+        np.testing.assert_array_equal(jj.cpu().numpy(), oracle.nearest(gb, y))
+        np.testing.assert_array_equal(counts.cpu().numpy(), oracle.counts_from_samples(ga, gb, x, y))
