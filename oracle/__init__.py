@@ -15,7 +15,11 @@ arXiv:1101.3228):
   the FP64 distance, ties to the lowest index;
 * ``counts_from_samples`` / ``transitions`` -- Algorithm III's counters p^k_ij;
 * ``backward`` / ``price`` -- the BDP recursion on the tree of Sec. 2 with
-  pi^k_ij = p^k_ij / p^k_i.
+  pi^k_ij = p^k_ij / p^k_i;
+* ``pathwise``      -- Algorithm II: every path simulated through all layers
+  (one search per layer), for the AR(1) chain or an Euler-scheme chain;
+* ``swing``         -- eq. (stochCtrl): the swing option's bang-bang BDP over
+  consumption states on the tree.
 
 Parity status of each function is recorded by the pin tests in
 ``tests/test_oracle_pins.py``; none is unpinned.
@@ -78,6 +82,8 @@ def _load():
             "qto_backward": (ctypes.c_int, [i32, P, P, P, P]),
             "qto_price_from_V": (ctypes.c_double, [P, P, P]),
             "qto_num_threads": (ctypes.c_int, []),
+            "qto_pathwise": (ctypes.c_int, [i32, i32, P, P, P, P, P, P, P, P, P, i64, i64, u64, i32, P, P, P]),
+            "qto_swing": (ctypes.c_int, [i32, P, P, P, i32, i32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -234,3 +240,63 @@ def price(N, counts_list, phi: np.ndarray) -> float:
     V = backward(N, counts_list, phi)
     c0 = np.ascontiguousarray(counts_list[0], dtype=np.int64)
     return float(_load().qto_price_from_V(_p(N), _p(c0), _p(V)))
+
+
+# --------------------------------------------------------------------------- Algorithm II and the swing option
+
+def pathwise(model, grids: np.ndarray, M: int, seed: int, prec: int, euler=None, m0: int = 0,
+             want_paths: bool = False):
+    """Algorithm II over all layers: list of per-layer counts (int64 [N_k, N_{k+1}]).
+
+    euler: None (the AR(1) chain) or (alpha, beta), each [n, d]: the innovation of
+    row l scaled by sqrt(max(alpha_l + beta_l x_l, 0)).  With want_paths the states
+    X [n+1, M, d] and cells [n+1, M] are returned too."""
+    N = np.ascontiguousarray(model.N, dtype=np.int64)
+    total = int(sum(int(N[k]) * int(N[k + 1]) for k in range(model.n)))
+    flat = np.zeros(total, dtype=np.int64)
+    arrs = [_f64(a) for a in (model.A, model.b, model.T, model.m, model.L)]
+    al = be = None
+    if euler is not None:
+        al = _f64(euler[0]).reshape(model.n, model.d)
+        be = _f64(euler[1]).reshape(model.n, model.d)
+    paths = cells = None
+    if want_paths:
+        paths = np.empty((model.n + 1, M, model.d), dtype=np.float64)
+        cells = np.empty((model.n + 1, M), dtype=np.int32)
+    g = _f64(grids)
+    _check(_load().qto_pathwise(model.d, model.n, _p(N), *[_p(a) for a in arrs],
+                                _p(al) if al is not None else None, _p(be) if be is not None else None,
+                                _p(g), m0, M, seed, prec, _p(flat),
+                                _p(paths) if want_paths else None, _p(cells) if want_paths else None),
+           "pathwise")
+    out, off = [], 0
+    for k in range(model.n):
+        sz = int(N[k]) * int(N[k + 1])
+        out.append(flat[off:off + sz].reshape(int(N[k]), int(N[k + 1])))
+        off += sz
+    if want_paths:
+        return out, paths, cells
+    return out
+
+
+def swing(N, counts_list, v: np.ndarray, Qmin: int, Qmax: int):
+    """Swing values P (concatenated Q-major blocks [Qmax+1, N_k]) and the price."""
+    N = np.ascontiguousarray(N, dtype=np.int64)
+    n = len(N) - 1
+    flat = _flat_counts(counts_list)
+    v = _f64(v)
+    P = np.empty(int(np.sum(N)) * (Qmax + 1), dtype=np.float64)
+    _check(_load().qto_swing(n, _p(N), _p(flat), _p(v), int(Qmin), int(Qmax), _p(P)), "swing")
+    c0 = np.ascontiguousarray(counts_list[0], dtype=np.int64)
+    price = float(_load().qto_price_from_V(_p(N), _p(c0), _p(np.ascontiguousarray(P[: int(N[0])]))))
+    return P, price
+
+
+def swing_blocks(N, P: np.ndarray, Qmax: int):
+    """Split the concatenated swing values into per-layer [Qmax+1, N_k] arrays."""
+    out, off = [], 0
+    for Nk in np.asarray(N, dtype=np.int64):
+        sz = int(Nk) * (Qmax + 1)
+        out.append(P[off:off + sz].reshape(Qmax + 1, int(Nk)))
+        off += sz
+    return out

@@ -18,6 +18,9 @@
  *                        j = NN(A_k X_k + T_k eps_k, Gamma_{k+1}), count p^k_ij;
  *   Algorithm I/III   -- pi^k_ij = p^k_ij / p^k_i;
  *   Sec. 2 (BDP on the tree) -- V_n = phi_n, V_k = max(phi_k, sum_j pi^k_ij V_{k+1}(j)).
+ *   Algorithm II      -- the path-wise estimator (each path through every layer,
+ *                        one search per layer), also for an Euler-scheme chain;
+ *   eq. (stochCtrl)   -- the swing option's bang-bang BDP over consumption states.
  *
  * Readings where the paper is silent (each is restated in the design notes):
  *   - distance and ties: the cell of z is argmin_i D64(z, x_i) with
@@ -620,6 +623,236 @@ double qto_price_from_V(const int64_t* N, const int64_t* counts, const double* V
         price = price + ((double)ci / (double)total) * V[i];
     }
     return price;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm II: the path-wise estimator (Sec. 3, Algorithms I and II)       */
+/* ------------------------------------------------------------------------ */
+/*
+ * Every path m is simulated layer after layer, as in Algorithms I and II:
+ *   X_0 = m_0 + L_0 z,  z = normals [0, d) of stream (m, layer 0);
+ *   for k = 0 .. n-1:
+ *     eps_k = normals [d, 2d) of stream (m, k);
+ *     X_{k+1} = b_k + A_k X_k + S_k(X_k) T_k eps_k;
+ *     j = NN(X_{k+1}, Gamma_{k+1});  p^k_ij += 1;  i <- j      (i_0 = NN(X_0, Gamma_0)).
+ * S_k = I is the AR(1) chain of Prop. 1.  The Euler-scheme chain (a chain that
+ * is not AR(1): its layers cannot be drawn independently, which is what
+ * Algorithm III needs) scales row l of the innovation by
+ *   s_{k,l}(x) = sqrt(max(alpha_{k,l} + beta_{k,l} x_l, 0)),
+ * the Euler step of a square-root diffusion dX = (drift) dt + sqrt(alpha + beta X) dW.
+ * In the sample precision, rounded one operation at a time in this order:
+ *   s_l = sqrt(max(alpha_l + beta_l * x_l, 0));  t_lq = s_l * T_lq;
+ *   acc = b_l; acc += A_lq * x_q (q = 0..d-1); acc += t_lq * eps_q (q = 0..l).
+ * (With the AR(1) chain t_lq = T_lq, which is also what s_l = 1 gives.)  The
+ * step of layer 0 is therefore the pair Algorithm III draws for layer 0.
+ */
+typedef struct {
+    float af[QTO_DMAX], bf[QTO_DMAX];
+    double ad[QTO_DMAX], bd[QTO_DMAX];
+    int on;
+} euler_params;
+
+static void load_euler(euler_params* E, int d, const double* alpha, const double* beta)
+{
+    E->on = alpha != NULL && beta != NULL;
+    for (int l = 0; l < d; ++l) {
+        E->ad[l] = E->on ? alpha[l] : 1.0;
+        E->bd[l] = E->on ? beta[l] : 0.0;
+        E->af[l] = (float)E->ad[l];
+        E->bf[l] = (float)E->bd[l];
+    }
+}
+
+/* One step of path m from state x (sample precision, widened) at layer k. */
+static void path_step(const layer_params* P, const euler_params* E, uint64_t seed, int32_t k, int64_t m,
+                      const double* x, double* xn)
+{
+    const int d = P->d;
+    if (P->prec == QTO_PREC_F32) {
+        float g[2 * QTO_DMAX], xf[QTO_DMAX], sc[QTO_DMAX];
+        normals_f32(seed, k, m, 2 * d, g);
+        for (int l = 0; l < d; ++l) xf[l] = (float)x[l];
+        for (int l = 0; l < d; ++l) {
+            float u = E->af[l] + E->bf[l] * xf[l];
+            sc[l] = sqrtf(u > 0.0f ? u : 0.0f);
+        }
+        for (int l = 0; l < d; ++l) {
+            float acc = P->bf[l];
+            for (int q = 0; q < d; ++q) acc = acc + P->Af[l * d + q] * xf[q];
+            for (int q = 0; q <= l; ++q) {
+                const float t = E->on ? sc[l] * P->Tf[l * d + q] : P->Tf[l * d + q];
+                acc = acc + t * g[d + q];
+            }
+            xn[l] = (double)acc;
+        }
+    } else {
+        double g[2 * QTO_DMAX], sc[QTO_DMAX];
+        normals_f64(seed, k, m, 2 * d, g);
+        for (int l = 0; l < d; ++l) {
+            double u = E->ad[l] + E->bd[l] * x[l];
+            sc[l] = sqrt(u > 0.0 ? u : 0.0);
+        }
+        for (int l = 0; l < d; ++l) {
+            double acc = P->bd[l];
+            for (int q = 0; q < d; ++q) acc = acc + P->Ad[l * d + q] * x[q];
+            for (int q = 0; q <= l; ++q) {
+                const double t = E->on ? sc[l] * P->Td[l * d + q] : P->Td[l * d + q];
+                acc = acc + t * g[d + q];
+            }
+            xn[l] = acc;
+        }
+    }
+}
+
+/* X_0 = m_0 + L_0 z of path m (z = normals [0, d) of stream (m, 0)). */
+static void path_start(const layer_params* P0, uint64_t seed, int64_t m, double* x)
+{
+    const int d = P0->d;
+    if (P0->prec == QTO_PREC_F32) {
+        float g[2 * QTO_DMAX];
+        normals_f32(seed, 0, m, d, g);
+        for (int l = 0; l < d; ++l) {
+            float acc = P0->mf[l];
+            for (int q = 0; q <= l; ++q) acc = acc + P0->Lf[l * d + q] * g[q];
+            x[l] = (double)acc;
+        }
+    } else {
+        double g[2 * QTO_DMAX];
+        normals_f64(seed, 0, m, d, g);
+        for (int l = 0; l < d; ++l) {
+            double acc = P0->md[l];
+            for (int q = 0; q <= l; ++q) acc = acc + P0->Ld[l * d + q] * g[q];
+            x[l] = acc;
+        }
+    }
+}
+
+/* Paths m0 .. m0+M-1 through layers 0..n.  counts: concatenated [N_k][N_{k+1}],
+ * accumulated (the caller zeroes them).  alpha/beta: [n][d] (both NULL: the
+ * AR(1) chain).  paths_out (optional): [n+1][M][d] FP64 states; cells_out
+ * (optional): [n+1][M] cells. */
+int qto_pathwise(int32_t d, int32_t n, const int64_t* N, const double* A, const double* b, const double* T,
+                 const double* m, const double* L, const double* alpha, const double* beta, const double* grids,
+                 int64_t m0, int64_t M, uint64_t seed, int32_t prec, int64_t* counts, double* paths_out,
+                 int32_t* cells_out)
+{
+    if (d < 1 || d > QTO_DMAX || n < 1 || M < 0) return QTO_EINVAL;
+    if ((alpha == NULL) != (beta == NULL)) return QTO_EINVAL;
+    int64_t* goff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 2));
+    int64_t* coff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    layer_params* LP = (layer_params*)malloc(sizeof(layer_params) * (size_t)(n + 1));
+    euler_params* EP = (euler_params*)malloc(sizeof(euler_params) * (size_t)(n + 1));
+    if (!goff || !coff || !LP || !EP) {
+        free(goff); free(coff); free(LP); free(EP);
+        return QTO_ENOMEM;
+    }
+    goff[0] = 0;
+    coff[0] = 0;
+    for (int32_t k = 0; k <= n; ++k) goff[k + 1] = goff[k] + N[k];
+    for (int32_t k = 0; k < n; ++k) coff[k + 1] = coff[k] + N[k] * N[k + 1];
+    /* layer k's step uses A_k, b_k, T_k; layer 0 also m_0, L_0 */
+    for (int32_t k = 0; k < n; ++k) {
+        load_layer(&LP[k], d, prec, m + (int64_t)k * d, L + (int64_t)k * d * d, A + (int64_t)k * d * d,
+                   b + (int64_t)k * d, T + (int64_t)k * d * d);
+        load_euler(&EP[k], d, alpha ? alpha + (int64_t)k * d : NULL, beta ? beta + (int64_t)k * d : NULL);
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < M; ++t) {
+        double x[QTO_DMAX], xn[QTO_DMAX];
+        const int64_t mm = m0 + t;
+        path_start(&LP[0], seed, mm, x);
+        int32_t i = nearest_one(d, grids, N[0], x);
+        if (paths_out) for (int l = 0; l < d; ++l) paths_out[t * d + l] = x[l];
+        if (cells_out) cells_out[t] = i;
+        for (int32_t k = 0; k < n; ++k) {
+            path_step(&LP[k], &EP[k], seed, k, mm, x, xn);
+            for (int l = 0; l < d; ++l) x[l] = xn[l];
+            const int32_t j = nearest_one(d, grids + goff[k + 1] * d, N[k + 1], x);
+            int64_t* cell = counts + coff[k] + (int64_t)i * N[k + 1] + j;
+#pragma omp atomic
+            *cell += 1;
+            if (paths_out) for (int l = 0; l < d; ++l) paths_out[((int64_t)(k + 1) * M + t) * d + l] = x[l];
+            if (cells_out) cells_out[(int64_t)(k + 1) * M + t] = j;
+            i = j;
+        }
+    }
+    free(goff); free(coff); free(LP); free(EP);
+    return QTO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Swing option on the tree (Sec. 2, eq. (stochCtrl) and its bang-bang BDP)  */
+/* ------------------------------------------------------------------------ */
+/*
+ * Controls q_k in {0, 1} at dates k = 0 .. n-1 (a bang-bang control exists, so
+ * the BDP runs over these two values), payoff q_k v_k(X_k), and the global
+ * constraint sum_k q_k in [Qmin, Qmax].  The state carries the consumption Q
+ * before date k.  Reading of the paper's I_Q and chi: chi(Q, x) = Q + x, and x
+ * is admissible at (k, Q) when the consumption can still end inside
+ * [Qmin, Qmax]:  F(k+1, Q + x)  with  F(k, Q) = (Q <= Qmax and Q + (n - k) >= Qmin).
+ *   P_n(., Q) = 0 where F(n, Q), -inf elsewhere;
+ *   P_k(i, Q) = max over admissible x of  x v_k(x_i) + sum_j pi^k_ij P_{k+1}(j, Q + x),
+ *               -inf where no x is admissible;  an empty row (p^k_i = 0) has
+ *               continuation 0.
+ * P: concatenated Q-major blocks, layer k = [Qmax + 1][N_k] at offset
+ * (Qmax + 1) * sum_{q<k} N_q.  v: concatenated [sum_k N_k] (layer n unused).
+ */
+static int swing_feasible(int32_t n, int32_t k, int64_t Q, int32_t Qmin, int32_t Qmax)
+{
+    return Q <= Qmax && Q + (n - k) >= Qmin;
+}
+
+int qto_swing(int32_t n, const int64_t* N, const int64_t* counts, const double* v, int32_t Qmin, int32_t Qmax,
+              double* P)
+{
+    if (n < 1 || Qmin < 0 || Qmax < Qmin) return QTO_EINVAL;
+    const int64_t nq = (int64_t)Qmax + 1;
+    int64_t* goff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 2));
+    int64_t* coff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    if (!goff || !coff) {
+        free(goff); free(coff);
+        return QTO_ENOMEM;
+    }
+    goff[0] = 0;
+    coff[0] = 0;
+    for (int32_t k = 0; k <= n; ++k) goff[k + 1] = goff[k] + N[k];
+    for (int32_t k = 0; k < n; ++k) coff[k + 1] = coff[k] + N[k] * N[k + 1];
+    double* Pn = P + nq * goff[n];
+    for (int64_t Q = 0; Q < nq; ++Q)
+        for (int64_t j = 0; j < N[n]; ++j)
+            Pn[Q * N[n] + j] = swing_feasible(n, n, Q, Qmin, Qmax) ? 0.0 : -INFINITY;
+    for (int32_t k = n - 1; k >= 0; --k) {
+        const int64_t Nk = N[k], Nk1 = N[k + 1];
+        const int64_t* ck = counts + coff[k];
+        const double* Pk1 = P + nq * goff[k + 1];
+        double* Pk = P + nq * goff[k];
+        const double* vk = v + goff[k];
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < Nk; ++i) {
+            int64_t ci = 0;
+            for (int64_t j = 0; j < Nk1; ++j) ci += ck[i * Nk1 + j];
+            for (int64_t Q = 0; Q < nq; ++Q) {
+                double best = -INFINITY;
+                for (int x = 0; x <= 1; ++x) {
+                    const int64_t Q1 = Q + x;
+                    if (!swing_feasible(n, k + 1, Q1, Qmin, Qmax)) continue;
+                    double cont = 0.0;
+                    if (ci > 0) {
+                        for (int64_t j = 0; j < Nk1; ++j) {
+                            const double pij = (double)ck[i * Nk1 + j] / (double)ci;
+                            cont = cont + pij * Pk1[Q1 * Nk1 + j];
+                        }
+                    }
+                    const double val = x ? vk[i] + cont : cont;
+                    if (val > best) best = val;
+                }
+                Pk[Q * Nk + i] = best;
+            }
+        }
+    }
+    free(goff);
+    free(coff);
+    return QTO_OK;
 }
 
 int qto_num_threads(void)
