@@ -190,6 +190,35 @@ QT_API qt_status qt_transitions(qt_ctx* ctx, const qt_model* model, const double
                          uint64_t seed, const qt_options* opts, void* counts, const qt_dump* dump,
                          qt_stats* stats, void* stream);
 
+/* Algorithm II (Sec. 3, Algorithms I and II): the path-wise estimator.  Every
+ * path m runs through all layers: X_0 = m_0 + L_0 z with z = normals [0, d)
+ * of stream (m, 0); for k = 0..n-1, eps_k = normals [d, 2d) of stream (m, k),
+ * X_{k+1} = b_k + A_k X_k + S_k(X_k) T_k eps_k, j = NN(X_{k+1}, Gamma_{k+1})
+ * and p^k_ij += 1 with i the cell of X_k.  One search per path and layer
+ * (Algorithm III makes two), sequential in k; the counts estimate the same
+ * pi^k_ij, and the first step is Algorithm III's layer-0 pair.
+ *   euler  NULL: the AR(1) chain of Prop. 1 (S_k = I).  Otherwise the Euler
+ *          step of a square-root diffusion, a chain that is not AR(1):
+ *          S_k = diag(s_kl), s_kl(x) = sqrt(max(alpha_kl + beta_kl x_l, 0)),
+ *          alpha, beta host FP64 [n][d].  In the sample precision, each
+ *          operation rounded in the order s_l = sqrt(max(alpha_l + beta_l*x_l, 0)),
+ *          t_lq = s_l*T_lq, acc = b_l, acc += A_lq*x_q (q ascending),
+ *          acc += t_lq*eps_q (q <= l).
+ *   opts   form QT_FORM_AUTO or QT_FORM_F32_RECHECK (FP32 screen with the exact
+ *          recheck: cells exact under the library contract); FP32 or FP64
+ *          samples.  Each grid's FP32 records must fit half of one CTA's
+ *          shared memory, else QT_EUNSUPPORTED.
+ *   counts, dump, stats as in qt_transitions (dump row k holds X_k, X_{k+1}
+ *          and their cells); model->m and L are read for layer 0 only.      */
+typedef struct {
+    const double* alpha;   /* host FP64 [n][d] */
+    const double* beta;    /* host FP64 [n][d] */
+} qt_euler;
+
+QT_API qt_status qt_transitions_pathwise(qt_ctx* ctx, const qt_model* model, const qt_euler* euler,
+                                         const double* grids, int64_t M, uint64_t seed, const qt_options* opts,
+                                         void* counts, const qt_dump* dump, qt_stats* stats, void* stream);
+
 /* Counting step of Algorithm III on caller-supplied samples (one layer pair):
  * counts[NA][NB] (dev, opts->counts_type) is OVERWRITTEN with
  * #{t : NN(X_t, gA) = i, NN(Y_t, gB) = j}.  gA dev FP64 [NA][d], gB [NB][d],
@@ -211,6 +240,28 @@ QT_API qt_status qt_counts_from_samples(qt_ctx* ctx, int32_t d, const double* gA
  *   phi, V dev FP64 [sum_k N_k] (V written)                                    */
 QT_API qt_status qt_backward(qt_ctx* ctx, int32_t n, const int64_t* N, const void* counts,
                       int32_t counts_type, const double* phi, double* V, void* stream);
+
+/* Swing option on the tree (Sec. 2, eq. (stochCtrl) and the bang-bang BDP that
+ * follows it): controls x_k in {0, 1} at dates k = 0..n-1, payoff x_k v_k(X_k),
+ * global constraint sum_k x_k in [Qmin, Qmax].  The paper leaves the
+ * admissible set I_Q and the transition chi of the consumption state Q to its
+ * reference; read here as chi(Q, x) = Q + x, and x admissible at (k, Q) when the
+ * consumption can still end inside [Qmin, Qmax]: F(k+1, Q + x) with
+ * F(k, Q) = (Q <= Qmax and Q + n - k >= Qmin).
+ *   P_n(., Q) = 0 where F(n, Q), -inf elsewhere;
+ *   P_k(i, Q) = max over admissible x of x v_k(i) + C_k(i, Q + x), -inf where
+ *               none is admissible;  C_k(i, Q') = (sum_j p^k_ij P_{k+1}(j, Q')) / p^k_i
+ *               in the fixed order of qt_backward (0 for an empty row).
+ * Qmax = 1, Qmin = 0 is the Bermudan of qt_backward with phi_n = 0, bit for bit.
+ *   N       host int64 [n+1];  counts dev, as in qt_backward
+ *   v       dev FP64 [sum_k N_k] payoff values (layer n unused)
+ *   P       dev FP64 [(Qmax + 1) * sum_k N_k], written: layer k is a Q-major
+ *           [Qmax + 1][N_k] block at offset (Qmax + 1) * sum_{q<k} N_q
+ *   price   host, optional: P_0(x_0, 0) if N_0 = 1, else sum_i (p^0_i / M) P_0(i, 0);
+ *           given, the call synchronises the stream.
+ * 0 <= Qmin <= min(Qmax, n), Qmax <= 2^20; QT_EINVAL otherwise.               */
+QT_API qt_status qt_swing(qt_ctx* ctx, int32_t n, const int64_t* N, const void* counts, int32_t counts_type,
+                          const double* v, int32_t Qmin, int32_t Qmax, double* P, double* price, void* stream);
 
 /* Forward step + backward induction + root value: the option price V^_0.
  * If N_0 = 1 the price is V_0(0); otherwise sum_i (p^0_i / M) V_0(i).

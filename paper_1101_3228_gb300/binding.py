@@ -28,7 +28,8 @@ FORM_NAMES = {FORM_AUTO: "auto", FORM_PLAIN_F64: "plain_f64", FORM_F32_RECHECK: 
 
 # every symbol include/qt.h declares (checked by the CPU test of the ABI)
 EXPORTS = ["qt_create", "qt_destroy", "qt_last_error", "qt_status_string", "qt_default_options",
-           "qt_build_grids", "qt_transitions", "qt_counts_from_samples", "qt_backward", "qt_price",
+           "qt_build_grids", "qt_transitions", "qt_transitions_pathwise", "qt_counts_from_samples",
+           "qt_backward", "qt_swing", "qt_price",
            "qt_get_status", "qt_transitions_workspace", "qt_counts_from_samples_noalloc",
            "qt_router_train", "qt_router_destroy", "qt_router_get_info", "qt_router_get_params",
            "qt_router_set_params", "qt_router_loss_grad"]
@@ -48,6 +49,10 @@ class QtOptions(ctypes.Structure):
 
 class QtDump(ctypes.Structure):
     _fields_ = [("count", i64), ("stride", i64), ("X", P), ("Y", P), ("i", P), ("j", P)]
+
+
+class QtEuler(ctypes.Structure):
+    _fields_ = [("alpha", P), ("beta", P)]
 
 
 class QtStats(ctypes.Structure):
@@ -81,9 +86,11 @@ _SIGS = {
     "qt_default_options": (None, [P]),
     "qt_build_grids": (i32, [P, P, i32, i64, i32, ctypes.c_double, u64, P, P]),
     "qt_transitions": (i32, [P, P, P, i64, u64, P, P, P, P, P]),
+    "qt_transitions_pathwise": (i32, [P, P, P, P, i64, u64, P, P, P, P, P]),
     "qt_counts_from_samples": (i32, [P, i32, P, i64, P, i64, P, P, i64, P, P, P, P, P, P]),
     "qt_backward": (i32, [P, i32, P, P, i32, P, P, P]),
     "qt_price": (i32, [P, P, P, i64, u64, P, P, P, P, P]),
+    "qt_swing": (i32, [P, i32, P, P, i32, P, i32, i32, P, P, P]),
     "qt_get_status": (i32, [P, P, P]),
     "qt_transitions_workspace": (i32, [P, P, P]),
     "qt_counts_from_samples_noalloc": (i32, [i32, P, i64, P, i64, P, P, i64, i32, P, P, P, P]),
@@ -236,6 +243,43 @@ class Context:
                                             _stream_ptr(stream)))
         return counts, stats, dump_t
 
+    def transitions_pathwise(self, model, grids, M: int, seed: int, opts: Optional[QtOptions] = None, euler=None,
+                             counts=None, dump_count: int = 0, dump_stride: int = 1, want_stats: bool = True,
+                             stream=None):
+        """Algorithm II counts (same layout as transitions), stats, dump.  euler: None (AR(1)
+        chain) or (alpha, beta) host arrays [n, d] of the Euler-scheme chain."""
+        import torch
+        hm = HostModel(model)
+        opts = opts or options()
+        dt = torch.int64 if opts.counts_type == COUNTS_I64 else torch.int32
+        dev = grids.device
+        if counts is None:
+            counts = torch.empty(hm.count_entries, dtype=dt, device=dev)
+        eu = None
+        keep = None
+        if euler is not None:
+            keep = [np.ascontiguousarray(euler[0], dtype=np.float64).reshape(hm.n, hm.d),
+                    np.ascontiguousarray(euler[1], dtype=np.float64).reshape(hm.n, hm.d)]
+            eu = QtEuler(keep[0].ctypes.data, keep[1].ctypes.data)
+        dump = None
+        dump_t = None
+        if dump_count > 0:
+            dump_t = dict(X=torch.empty((hm.n, dump_count, hm.d), dtype=torch.float64, device=dev),
+                          Y=torch.empty((hm.n, dump_count, hm.d), dtype=torch.float64, device=dev),
+                          i=torch.empty((hm.n, dump_count), dtype=torch.int32, device=dev),
+                          j=torch.empty((hm.n, dump_count), dtype=torch.int32, device=dev))
+            dump = QtDump(dump_count, dump_stride, _ptr(dump_t["X"]), _ptr(dump_t["Y"]), _ptr(dump_t["i"]),
+                          _ptr(dump_t["j"]))
+        stats = QtStats() if want_stats else None
+        self._check(self.lib.qt_transitions_pathwise(self.h, ctypes.byref(hm.c),
+                                                     ctypes.byref(eu) if eu is not None else None, _ptr(grids),
+                                                     int(M), int(seed), ctypes.byref(opts), _ptr(counts),
+                                                     ctypes.byref(dump) if dump is not None else None,
+                                                     ctypes.byref(stats) if stats is not None else None,
+                                                     _stream_ptr(stream)))
+        del keep
+        return counts, stats, dump_t
+
     def counts_from_samples(self, gA, gB, X, Y, opts: Optional[QtOptions] = None, want_cells: bool = False,
                             stream=None):
         import torch
@@ -261,6 +305,16 @@ class Context:
         self._check(self.lib.qt_backward(self.h, len(Nh) - 1, Nh.ctypes.data, _ptr(counts), counts_type,
                                          _ptr(phi), _ptr(V), _stream_ptr(stream)))
         return V
+
+    def swing(self, N, counts, v, Qmin: int, Qmax: int, counts_type: int = COUNTS_I64, stream=None):
+        """Swing values P (flat, Q-major blocks [Qmax+1, N_k] per layer) and the price."""
+        import torch
+        Nh = np.ascontiguousarray(N, dtype=np.int64)
+        P_ = torch.empty(int(np.sum(Nh)) * (Qmax + 1), dtype=torch.float64, device=v.device)
+        out = ctypes.c_double(0.0)
+        self._check(self.lib.qt_swing(self.h, len(Nh) - 1, Nh.ctypes.data, _ptr(counts), counts_type, _ptr(v),
+                                      int(Qmin), int(Qmax), _ptr(P_), ctypes.byref(out), _stream_ptr(stream)))
+        return P_, out.value
 
     def price(self, model, grids, M: int, seed: int, phi, opts: Optional[QtOptions] = None, stream=None):
         """grids / phi may be torch CUDA tensors or host numpy arrays (copied in by the library)."""

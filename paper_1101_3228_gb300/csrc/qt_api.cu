@@ -23,6 +23,9 @@ __global__ void prep_records_kernel(const double*, GridInfo*, int, int, int, int
 __global__ void backward_layer_kernel(const void*, int, long long, int, int, const double*, const double*, double*);
 __global__ void root_price_kernel(const void*, int, int, int, const double*, double*);
 __global__ void fold_status_kernel(const DevStatus*, DevStatus*);
+__global__ void swing_terminal_kernel(int, int, int, int, double*);
+__global__ void swing_layer_kernel(const void*, int, long long, int, int, const double*, const double*, double*, int,
+                                   int, int, int);
 __global__ void kmeans_draw_kernel(int, unsigned long long, long long, float*);
 __global__ void kmeans_assign_kernel(int, long long, const float*, int, const float*, unsigned long long*,
                                      unsigned long long*, int);
@@ -309,6 +312,7 @@ struct Plan {
     long long tc_chunk_items = 0;      // tensor-core form: work items per draw pass
     size_t tc_item_bytes = 0;          // tensor-core form: drawn-sample bytes per work item
     int d = 0, n = 0, ngrids = 0;
+    int euler = 0;                     // path-wise form: Euler-scheme chain
     long long total_recs = 0;
     size_t grid_bytes = 0, hist_bytes = 0, dyn_smem = 0;
     long long total_items = 0;
@@ -331,7 +335,7 @@ struct FwdIO {
 };
 
 qt_status make_plan_full(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, long long M,
-                         const qt_options* o, bool from_arrays, Plan& P);
+                         const qt_options* o, bool from_arrays, Plan& P, int algo);
 
 // Work items per draw/forward pass of the tensor-core form: as many as 2 GiB of
 // drawn samples hold, or fewer when the caller caps it.
@@ -347,9 +351,10 @@ long long tc_chunk(const Plan& P, const qt_options* o)
 // its global index, which also keys the sampler's counters) but get no work
 // items, and layer k's counts start at offset 0 of the counts buffer.
 qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, long long M, const qt_options* o,
-                    bool from_arrays, Plan& P, int only_layer = -1)
+                    bool from_arrays, Plan& P, int only_layer = -1, int algo = 3)
 {
-    qt_status s = make_plan_full(ctx, d, n, Ns, mus, M, o, from_arrays, P);
+    qt_status s = make_plan_full(ctx, d, n, Ns, mus, M, o, from_arrays, P, algo);
+    if (!s && algo == 2 && only_layer >= 0) return fail(ctx, QT_EUNSUPPORTED, "the path-wise form runs every layer");
     if (s || only_layer < 0) return s;
     if (only_layer >= n) return fail(ctx, QT_EINVAL, "layer %d of %d", only_layer, n);
     const int items = P.layers[only_layer].items;
@@ -365,14 +370,22 @@ qt_status make_plan(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* 
 }
 
 // Pick form, dimension class, tile and shared memory for a problem described
-// by grid sizes Ns (n+1 entries) and centres mus ((n+1) x d).
+// by grid sizes Ns (n+1 entries) and centres mus ((n+1) x d).  algo = 3 is
+// Algorithm III (independent layer pairs), algo = 2 Algorithm II (paths).
 qt_status make_plan_full(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, long long M,
-                         const qt_options* o, bool from_arrays, Plan& P)
+                         const qt_options* o, bool from_arrays, Plan& P, int algo)
 {
     P.d = d;
     P.n = n;
     P.dm = dm_for(d);
     int form = o->form;
+    if (algo == 2) {
+        // the path-wise form screens in FP32 with the exact recheck
+        if (form != QT_FORM_AUTO && form != QT_FORM_F32_RECHECK)
+            return fail(ctx, QT_EUNSUPPORTED, "the path-wise form supports the FP32 screen only (form %d)", form);
+        if (from_arrays) return fail(ctx, QT_EUNSUPPORTED, "the path-wise form draws its own paths");
+        form = QT_FORM_F32_RECHECK;
+    }
     // automatic choice: the fastest certified form measured on GB300 -- the
     // tensor-core screen for 3 <= d <= 10, the FP32 screen otherwise
     if (form == QT_FORM_AUTO) form = (d >= 3 && d <= 10) ? QT_FORM_TC_RECHECK : QT_FORM_F32_RECHECK;
@@ -399,7 +412,7 @@ qt_status make_plan_full(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
         return fail(ctx, QT_EINVAL, "sample_prec %d", o->sample_prec);
     P.rec_floats = rec_floats_for(P.dm);
     P.rec64 = rec64_for(P.dm);
-    P.pstride = (int)round_up(2 * d + 3 * d * d, 4);
+    P.pstride = param_stride(d);
     P.ngrids = n + 1;
     P.grids.resize(P.ngrids);
     long long goff = 0, roff = 0;
@@ -419,6 +432,50 @@ qt_status make_plan_full(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
         roff += G.Npad;
     }
     P.total_recs = roff;
+    if (algo == 2) {
+        // Algorithm II: a CTA carries a tile of paths through every layer; the
+        // FP32 records of one grid per shared-memory buffer, two buffers
+        const bool f32 = o->sample_prec == QT_PREC_F32;
+        P.form = kPathwise;
+        const size_t rec_bytes = (size_t)P.rec_floats * 4;
+        size_t gmax = 0;
+        for (int g = 0; g <= n; ++g) gmax = std::max(gmax, (size_t)P.grids[g].Npad * rec_bytes);
+        const size_t budget = ctx->smem_optin > 24 * 1024 ? ctx->smem_optin - 24 * 1024 : 0;
+        P.grid_bytes = 2 * round_up((long long)gmax, 128);
+        if (P.grid_bytes > budget)
+            return fail(ctx, QT_EUNSUPPORTED,
+                        "the path-wise form keeps two grids in shared memory: %zu bytes exceed %zu", P.grid_bytes,
+                        budget);
+        int S = o->tile_samples_per_thread > 0 ? o->tile_samples_per_thread : pathwise_default_spt(P.dm, f32);
+        if (!pathwise_variant_exists(P.dm, S, f32))
+            return fail(ctx, QT_EUNSUPPORTED, "no path-wise kernel for d %d, %d paths per thread", d, S);
+        P.S = S;
+        P.block = 256;
+        P.tile = P.block * S;
+        P.hist_bytes = 0;
+        P.dyn_smem = P.grid_bytes;
+        P.layers.resize(n);
+        long long coff = 0;
+        for (int k = 0; k < n; ++k) {
+            LayerDesc& L = P.layers[k];
+            memset(&L, 0, sizeof L);
+            L.NA = (int)Ns[k];
+            L.NB = (int)Ns[k + 1];
+            L.NApad = P.grids[k].Npad;
+            L.NBpad = P.grids[k + 1].Npad;
+            L.gridA = k;
+            L.gridB = k + 1;
+            L.goffA = P.grids[k].goff;
+            L.goffB = P.grids[k + 1].goff;
+            L.roffA = P.grids[k].roff;
+            L.roffB = P.grids[k + 1].roff;
+            L.coff = coff;
+            coff += (long long)L.NA * L.NB;
+        }
+        P.total_items = (M + P.tile - 1) / P.tile;
+        P.count_entries = coff;
+        return QT_OK;
+    }
     if (P.form == kRouterCert) {
         P.S = 1;
         P.block = 128;
@@ -642,6 +699,7 @@ qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long
     fp.smem_hist_entries = (int)(P.hist_bytes / 4);
     fp.seg_records = P.seg_records;
     fp.spin_budget = o->spin_budget == 0 ? (1ll << 26) : o->spin_budget;
+    fp.pathwise_euler = P.euler;
     fp.layers = (const LayerDesc*)dlayers;
     fp.grids = (const GridInfo*)dgrids;
     fp.params_f = (const float*)dparams_f;
@@ -788,6 +846,7 @@ qt_status run_plan(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long M, uns
         key_append(key, &P.S, sizeof P.S);
         key_append(key, &P.streamed, sizeof P.streamed);
         key_append(key, &P.seg_records, sizeof P.seg_records);
+        key_append(key, &P.euler, sizeof P.euler);
         key_append(key, &M, sizeof M);
         key_append(key, &seed, sizeof seed);
         key_append(key, &source, sizeof source);
@@ -902,7 +961,7 @@ TuneKey tune_key(const Plan& P, int prec, const int64_t* Ns, int n)
 // Shared body of qt_transitions and qt_counts_from_samples.
 qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, const double* params_d_host,
                          long long M, unsigned long long seed, const qt_options* o, int source, const FwdIO& io,
-                         qt_stats* stats, cudaStream_t st, int only_layer = -1)
+                         qt_stats* stats, cudaStream_t st, int only_layer = -1, int algo = 3, int euler = 0)
 {
     qt_options oi;
     if (only_layer >= 0 && only_layer == injected_timeout_layer()) {
@@ -911,11 +970,12 @@ qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
         o = &oi;
     }
     Plan P;
-    qt_status s = make_plan(ctx, d, n, Ns, mus, M, o, source == kArrays, P, only_layer);
+    qt_status s = make_plan(ctx, d, n, Ns, mus, M, o, source == kArrays, P, only_layer, algo);
     if (s) return s;
+    P.euler = euler;
     const bool capturing = stream_is_capturing(st);
-    if (P.form != kTcRecheck && P.form != kRouterCert && o->tile_samples_per_thread <= 0 && !(o->flags & QT_FLAG_NO_TUNE) && !capturing &&
-        o->spin_budget >= 0) {
+    if (P.form != kTcRecheck && P.form != kRouterCert && P.form != kPathwise && o->tile_samples_per_thread <= 0 &&
+        !(o->flags & QT_FLAG_NO_TUNE) && !capturing && o->spin_budget >= 0) {
         const TuneKey key = tune_key(P, source == kArrays ? 0 : o->sample_prec, Ns, n);
         if (!ctx->tune.count(key)) {
             if ((s = autotune(ctx, d, n, Ns, mus, params_d_host, M, seed, o, source, io, P, key, st))) return s;
@@ -933,12 +993,13 @@ qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
     // one layer at a time (fused backward) launches directly: each layer would be a new graph
     const bool use_graph = !(o->flags & QT_FLAG_NO_GRAPH) && !capturing && only_layer < 0;
     if ((s = run_plan(ctx, P, io, M, seed, o, source, params_d_host, st, use_graph, ""))) return s;
-    if (stats) return read_status(ctx, st, stats, (long long)n * M, 2ll * n * M);
+    if (stats) return read_status(ctx, st, stats, (long long)n * M, (algo == 2 ? n + 1ll : 2ll * n) * M);
     return QT_OK;
 }
 
-// Pack m, b, L, A, T of layer k (FP64) in the order the sampler reads them.
-void pack_params(const qt_model* m, int k, int pstride, double* out)
+// Pack m, b, L, A, T of layer k (FP64) in the order the sampler reads them,
+// then the Euler-scheme scaling alpha, beta (1 and 0 without one).
+void pack_params(const qt_model* m, const qt_euler* eu, int k, int pstride, double* out)
 {
     const int d = m->d;
     double* p = out + (long long)k * pstride;
@@ -949,6 +1010,10 @@ void pack_params(const qt_model* m, int k, int pstride, double* out)
         p[2 * d + e] = c <= r ? m->L[(long long)k * d * d + e] : 0.0;
         p[2 * d + d * d + e] = m->A[(long long)k * d * d + e];
         p[2 * d + 2 * d * d + e] = c <= r ? m->T[(long long)k * d * d + e] : 0.0;
+    }
+    for (int l = 0; l < d; ++l) {
+        p[2 * d + 3 * d * d + l] = eu ? eu->alpha[(long long)k * d + l] : 1.0;
+        p[3 * d + 3 * d * d + l] = eu ? eu->beta[(long long)k * d + l] : 0.0;
     }
 }
 
@@ -989,9 +1054,9 @@ qt_status transitions_impl(qt_ctx* ctx, const qt_model* model, const double* gri
     }
     DeviceGuard g(ctx->device);
     const int d = model->d, n = model->n;
-    const int pstride = (int)round_up(2 * d + 3 * d * d, 4);
+    const int pstride = param_stride(d);
     std::vector<double> params((size_t)n * pstride, 0.0);
-    for (int k = 0; k < n; ++k) pack_params(model, k, pstride, params.data());
+    for (int k = 0; k < n; ++k) pack_params(model, nullptr, k, pstride, params.data());
     FwdIO io;
     memset(&io, 0, sizeof io);
     io.g64 = grids;
@@ -1001,6 +1066,40 @@ qt_status transitions_impl(qt_ctx* ctx, const qt_model* model, const double* gri
                           (cudaStream_t)stream, only_layer);
 }
 }  // namespace
+
+extern "C" qt_status qt_transitions_pathwise(qt_ctx* ctx, const qt_model* model, const qt_euler* euler,
+                                             const double* grids, int64_t M, uint64_t seed, const qt_options* opts,
+                                             void* counts, const qt_dump* dump, qt_stats* stats, void* stream)
+{
+    if (!ctx) return QT_EINVAL;
+    qt_status s = validate_model(ctx, model);
+    if (s) return s;
+    if (!grids || !counts) return fail(ctx, QT_EINVAL, "grids or counts is NULL");
+    if (M < 1 || M > 0xFFFFFFFFll) return fail(ctx, QT_EINVAL, "M = %lld outside [1, 2^32)", (long long)M);
+    if (euler && (!euler->alpha || !euler->beta)) return fail(ctx, QT_EINVAL, "euler needs alpha and beta");
+    qt_options o;
+    if (opts) o = *opts; else qt_default_options(&o);
+    if (o.counts_type != QT_COUNTS_I64 && o.counts_type != QT_COUNTS_U32)
+        return fail(ctx, QT_EINVAL, "counts_type %d", o.counts_type);
+    if (o.sample_prec != QT_PREC_F32 && o.sample_prec != QT_PREC_F64)
+        return fail(ctx, QT_EINVAL, "sample_prec %d", o.sample_prec);
+    if (dump && dump->count > 0) {
+        if (dump->stride < 1 || !dump->X || !dump->Y || !dump->i || !dump->j)
+            return fail(ctx, QT_EINVAL, "dump needs stride >= 1 and four buffers");
+    }
+    DeviceGuard g(ctx->device);
+    const int d = model->d, n = model->n;
+    const int pstride = param_stride(d);
+    std::vector<double> params((size_t)n * pstride, 0.0);
+    for (int k = 0; k < n; ++k) pack_params(model, euler, k, pstride, params.data());
+    FwdIO io;
+    memset(&io, 0, sizeof io);
+    io.g64 = grids;
+    io.counts = counts;
+    io.dump = (dump && dump->count > 0) ? dump : nullptr;
+    return forward_common(ctx, d, n, model->N, model->m, params.data(), M, seed, &o, kSampler, io, stats,
+                          (cudaStream_t)stream, -1, 2, euler ? 1 : 0);
+}
 
 extern "C" qt_status qt_counts_from_samples(qt_ctx* ctx, int32_t d, const double* gA, int64_t NA, const double* gB,
                                             int64_t NB, const double* X, const double* Y, int64_t M,
@@ -1054,7 +1153,7 @@ extern "C" qt_status qt_transitions_workspace(const qt_model* model, const qt_op
     const int d = model->d, n = model->n, dm = dm_for(d);
     long long recs = 0;
     for (int k = 0; k <= n; ++k) recs += round_up(model->N[k], kChunk);
-    const long long pstride = round_up(2 * d + 3 * d * d, 4);
+    const long long pstride = param_stride(d);
     size_t b = sizeof(LayerDesc) * n + sizeof(GridInfo) * (n + 1) + (size_t)n * pstride * 12 + sizeof(DevStatus);
     b += o.form == QT_FORM_PLAIN_F64 ? (size_t)recs * rec64_for(dm) * 8 : (size_t)recs * rec_floats_for(dm) * 4;
     *bytes = b;
@@ -1085,6 +1184,46 @@ extern "C" qt_status qt_backward(qt_ctx* ctx, int32_t n, const int64_t* N, const
         backward_layer_kernel<<<(unsigned)((threads + blk - 1) / blk), blk, 0, st>>>(
             counts, u32, coff[k], (int)N[k], (int)N[k + 1], phi + goff[k], V + goff[k + 1], V + goff[k]);
         QT_CUDA(cudaGetLastError());
+    }
+    return QT_OK;
+}
+
+extern "C" qt_status qt_swing(qt_ctx* ctx, int32_t n, const int64_t* N, const void* counts, int32_t counts_type,
+                              const double* v, int32_t Qmin, int32_t Qmax, double* P, double* price, void* stream)
+{
+    if (!ctx) return QT_EINVAL;
+    if (n < 1 || !N || !counts || !v || !P) return fail(ctx, QT_EINVAL, "bad arguments to qt_swing");
+    if (counts_type != QT_COUNTS_I64 && counts_type != QT_COUNTS_U32)
+        return fail(ctx, QT_EINVAL, "counts_type %d", counts_type);
+    if (Qmin < 0 || Qmax < Qmin || Qmin > n || Qmax > (1 << 20))
+        return fail(ctx, QT_EINVAL, "volume constraint [%d, %d] with n = %d", Qmin, Qmax, n);
+    for (int k = 0; k <= n; ++k)
+        if (N[k] < 1 || N[k] > (1 << 24)) return fail(ctx, QT_EINVAL, "N[%d]", k);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nq = (long long)Qmax + 1;
+    std::vector<long long> goff(n + 2, 0), coff(n + 1, 0);
+    for (int k = 0; k <= n; ++k) goff[k + 1] = goff[k] + N[k];
+    for (int k = 0; k < n; ++k) coff[k + 1] = coff[k] + N[k] * N[k + 1];
+    const long long tn = nq * N[n];
+    swing_terminal_kernel<<<(unsigned)((tn + 255) / 256), 256, 0, st>>>((int)N[n], n, Qmin, Qmax, P + nq * goff[n]);
+    QT_CUDA(cudaGetLastError());
+    const int u32 = counts_type == QT_COUNTS_U32;
+    for (int k = n - 1; k >= 0; --k) {
+        const long long threads = (long long)N[k] * 32;
+        swing_layer_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+            counts, u32, coff[k], (int)N[k], (int)N[k + 1], v + goff[k], P + nq * goff[k + 1], P + nq * goff[k], n,
+            k, Qmin, Qmax);
+        QT_CUDA(cudaGetLastError());
+    }
+    if (price) {
+        void* dout;
+        qt_status s = dev_get(ctx, "swing_out", sizeof(double), &dout);
+        if (s) return s;
+        root_price_kernel<<<1, 32, 0, st>>>(counts, u32, (int)N[0], (int)N[1], P, (double*)dout);
+        QT_CUDA(cudaGetLastError());
+        QT_CUDA(cudaMemcpyAsync(price, dout, sizeof(double), cudaMemcpyDeviceToHost, st));
+        QT_CUDA(cudaStreamSynchronize(st));
     }
     return QT_OK;
 }

@@ -8,8 +8,13 @@ constexpr int kDMax = 16;          // largest state dimension
 constexpr int kChunk = 16;         // candidates per min-tracking chunk of the FP32 screen
 constexpr int kSlots = 2;          // ring slots of the streamed-grid mode
 
-enum Form : int32_t { kPlainF64 = 1, kF32Recheck = 2, kTcRecheck = 3, kRouterCert = 4 };
+enum Form : int32_t { kPlainF64 = 1, kF32Recheck = 2, kTcRecheck = 3, kRouterCert = 4, kPathwise = 5 };
 enum Source : int32_t { kSampler = 0, kArrays = 1 };
+
+// Per-layer sampler parameters packed by the host: m[d], b[d], L[d*d], A[d*d],
+// T[d*d] (read by every form) and alpha[d], beta[d] (the Euler-scheme chain of
+// the path-wise form), padded to a multiple of 4 entries.
+__host__ __device__ constexpr int param_stride(int d) { return (4 * d + 3 * d * d + 3) / 4 * 4; }
 
 // Device status block, zeroed before every forward call.
 struct DevStatus {
@@ -85,6 +90,7 @@ struct ForwardParams {
     int32_t smem_hist_entries;     // u32 entries reserved for the private histogram
     int32_t seg_records;           // streamed mode: records per ring slot (multiple of kChunk)
     long long spin_budget;         // bounded waits; < 0: give up at once
+    int32_t pathwise_euler;        // Algorithm II: 1 = Euler-scheme chain (innovation rows scaled)
     // tables
     const LayerDesc* layers;
     const GridInfo* grids;

@@ -111,6 +111,74 @@ __global__ void backward_layer_kernel(const void* __restrict__ counts, int u32, 
     }
 }
 
+// ------------------------------------------------------------------ swing option
+//
+// Eq. (stochCtrl) with the bang-bang BDP of Sec. 2: controls x in {0, 1} at
+// dates k = 0..n-1, consumption state Q, chi(Q, x) = Q + x, x admissible at
+// (k, Q) when F(k+1, Q + x), F(k, Q) = (Q <= Qmax and Q + n - k >= Qmin):
+//   P_k(i, Q) = max over admissible x of x v_k(i) + C_k(i, Q + x),
+//   C_k(i, Q') = (sum_j p^k_ij P_{k+1}(j, Q')) / p^k_i   (0 for an empty row),
+// -inf where no x is admissible.  P blocks are Q-major: [Qmax + 1][N].  One
+// warp per row i walks Q upwards and carries C(i, Q + 1) to the next Q, so each
+// continuation is summed once, in the order of backward_layer_kernel (lanes
+// j mod 32 ascending, then the fixed butterfly), which makes the one-right
+// swing (Qmax = 1) the Bermudan of qt_backward bit for bit.
+__device__ __forceinline__ bool swing_feasible(int n, int k, int Q, int Qmin, int Qmax)
+{
+    return Q <= Qmax && Q + (n - k) >= Qmin;
+}
+
+__global__ void swing_terminal_kernel(int Nn, int n, int Qmin, int Qmax, double* __restrict__ Pn)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)(Qmax + 1) * Nn) return;
+    const int Q = (int)(e / Nn);
+    Pn[e] = swing_feasible(n, n, Q, Qmin, Qmax) ? 0.0 : __longlong_as_double(0xFFF0000000000000LL);
+}
+
+__global__ void swing_layer_kernel(const void* __restrict__ counts, int u32, long long coff, int Nk, int Nk1,
+                                   const double* __restrict__ vk, const double* __restrict__ Pnext,
+                                   double* __restrict__ Pk, int n, int k, int Qmin, int Qmax)
+{
+    const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= Nk) return;
+    const long long row = coff + (long long)warp * Nk1;
+    const uint32_t* c32 = reinterpret_cast<const uint32_t*>(counts) + row;
+    const long long* c64 = reinterpret_cast<const long long*>(counts) + row;
+    long long ci = 0;
+    for (int j = lane; j < Nk1; j += 32) ci += u32 ? (long long)c32[j] : c64[j];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) ci += __shfl_xor_sync(0xFFFFFFFFu, ci, off);
+    const double ninf = __longlong_as_double(0xFFF0000000000000LL);
+    // continuation C(i, Q') for a feasible Q' at date k + 1
+    auto cont = [&](int Qp) -> double {
+        if (!swing_feasible(n, k + 1, Qp, Qmin, Qmax)) return ninf;
+        const double* Pq = Pnext + (long long)Qp * Nk1;
+        double acc = 0.0;
+        for (int j = lane; j < Nk1; j += 32) {
+            const double cv = u32 ? (double)c32[j] : (double)c64[j];
+            acc = __dadd_rn(acc, __dmul_rn(cv, Pq[j]));
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, off));
+        return ci == 0 ? 0.0 : __ddiv_rn(acc, (double)ci);
+    };
+    const double v = vk[warp];
+    double c_cur = cont(0);
+    for (int Q = 0; Q <= Qmax; ++Q) {
+        const double c_next = Q + 1 <= Qmax ? cont(Q + 1) : ninf;
+        double best = ninf;
+        if (swing_feasible(n, k + 1, Q, Qmin, Qmax)) best = c_cur;                  // x = 0
+        if (swing_feasible(n, k + 1, Q + 1, Qmin, Qmax)) {                          // x = 1
+            const double val = __dadd_rn(v, c_next);
+            if (val > best) best = val;
+        }
+        if (lane == 0) Pk[(long long)Q * Nk + warp] = best;
+        c_cur = c_next;
+    }
+}
+
 // Status of one launch folded into an accumulator (the fused price mode runs
 // one launch per layer pair, each clearing its own status block): the first
 // error code and site are kept, the counters are summed.  One thread.
