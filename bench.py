@@ -4,10 +4,15 @@ Wilbertz, arXiv:1101.3228) on GB300.
 Metric: certified sample.layers/s -- M pairs per layer times n layers divided
 by the device time of one qt_transitions call (counts exact under the FP64
 contract, ready on the device).  A step is one whole forward step over all
-layers.  Default workload: the 2-factor OU model (d = 2, n = 100 daily layers,
-N_k = 500 product grids, M = 10^7 pairs per layer).
+layers.  Default workload: the largest one whose step is a few seconds, the
+8-d AR(1) chain at full size (d = 8, n = 50, N_k = 4000, M = 10^8 pairs per
+layer), in the automatic form (the tensor-core screen).  Extra keys: the 10-d
+365-layer chain at full size (M = 10^8, two timed steps), the 4-d basket at
+full size, the 2-factor OU workload (the FP32 screen, Algorithm II, the swing
+option's backward induction) and the paper's own scenario.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME] [--impl ours|reference]
+                    [--no-extras]
 
 Prints one JSON line on rank 0.  With torchrun, every rank runs an independent
 replica with its own seed (weak scaling, no collective on the data path).
@@ -43,9 +48,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="ou2", choices=list(W.BUILDERS))
+    ap.add_argument("--config", default="ar8", choices=list(W.BUILDERS))
     ap.add_argument("--form", default="auto")
-    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--no-extras", action="store_true", help="skip the extra workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--M", type=int, default=0, help="override samples per layer")
@@ -79,34 +85,27 @@ def plain_form(model, B):
     return B.FORM_PLAIN_F64 if model.d <= 2 else B.FORM_F32_RECHECK
 
 
+def candidates_per_sample_layer(model):
+    """Brute-force candidate distances per sample.layer: N_k + N_{k+1}, averaged over layers."""
+    N = np.asarray(model.N, dtype=np.float64)
+    return float(np.sum(N[:-1] + N[1:]) / model.n)
+
+
 def flops_per_sample_layer(model):
-    """Algorithmic FP32 work of the brute-force screen: per candidate d fused
-    multiply-adds (2d flops) and one comparison (Sec. 4 counts 6 operations per
-    2-d distance with 3 additions, 2 multiplications and 1 comparison)."""
-    N = np.asarray(model.N, dtype=np.float64)
-    cand = np.sum(N[:-1] + N[1:]) / model.n
-    return float(cand * (2 * model.d + 1))
+    """Algorithmic work of the search: per candidate distance d subtractions (or
+    the expanded form's d multiply-adds) and d multiply-adds, 2d flops (Sec. 4
+    counts 6 operations for a 2-d distance including its comparison; the
+    comparison is not counted here)."""
+    return candidates_per_sample_layer(model) * 2 * model.d
 
 
-def tc_flops_per_sample_layer(model):
-    """Useful tensor-core work of the tensor-core screen: per candidate one dot
-    product of the 3d + 2 operand columns that carry data (FP16 head/tail split of
-    sample and grid point, plus the squared norm), 2 flops each."""
-    N = np.asarray(model.N, dtype=np.float64)
-    cand = np.sum(N[:-1] + N[1:]) / model.n
-    return float(cand * (3 * model.d + 2) * 2)
-
-
-def tc_launches_per_step(model):
-    """Kernels the tensor-core form launches per step: record and operand-tile
-    preparation, then a draw pass and a forward pass per chunk of work items (the
-    library draws up to 2 GiB of samples per chunk)."""
+def tc_pipe_flops_per_sample_layer(model):
+    """Work the tensor pipe does for the tensor-core screen: per candidate a dot
+    product over all K operand columns (the FP16 head/tail split of sample and grid
+    point, the squared norm, zero padding), 2 flops each."""
     dm = 2 if model.d <= 2 else (4 if model.d <= 4 else (6 if model.d <= 6 else (8 if model.d <= 8 else 10)))
     K = 16 if dm <= 4 else 32
-    item_bytes = 2 * 128 * K * 2 + 2 * (dm + 1) * 128 * 4
-    items = model.n * ((model.M + 127) // 128)
-    chunk = max(1, min(items, (2 << 30) // item_bytes))
-    return 2 + 2 * ((items + chunk - 1) // chunk)
+    return candidates_per_sample_layer(model) * 2 * K
 
 
 def replica_seed(model, rank: int) -> int:
@@ -255,6 +254,139 @@ def run_reference(args, model, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def bench_grids(ctx, B, model):
+    """The benchmark's grids, built by the library: product grids of 1-d stationary
+    quantizers for the 2-factor model, sample Lloyd on seeded Gaussian draws otherwise."""
+    return ctx.build_grids(model, grid_method(model), samples=max(20 * int(np.max(model.N)), 200000), iters=20,
+                           seed=W.GRID_SEED_BASE + W.CONFIG_INDEX.get(model.name, 9))
+
+
+def counts_type_for(B, model, dev):
+    """int64 counts unless they would take more than a quarter of the device (then uint32)."""
+    import torch
+    big = model.count_entries * 8 > torch.cuda.get_device_properties(dev).total_memory // 4
+    return B.COUNTS_U32 if big else B.COUNTS_I64
+
+
+def tensor_roofline(model, units, kern_ms, peaks):
+    """Tensor-core screen against the measured dense 16-bit tensor rate (FP16 runs at
+    the bf16 rate on this part), sustained figure: the algorithmic work (2d flops per
+    candidate) and, beside it, the pipe's share (K operand columns per candidate)."""
+    tpeak = peaks.get("bf16_tflops_sustained", 1700.0)
+    sec = kern_ms / 1e3
+    ach = flops_per_sample_layer(model) * units / sec / 1e12
+    pipe = tc_pipe_flops_per_sample_layer(model) * units / sec / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s", "frac": ach / tpeak,
+            "mma_frac": pipe / tpeak, "kernel_ms": kern_ms,
+            "work": f"{flops_per_sample_layer(model):.0f} flops per sample.layer "
+                    f"(2d per candidate, {candidates_per_sample_layer(model):.0f} candidates)",
+            "peak_basis": "measured dense bf16 GEMM, sustained (of measured)"
+            if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)"}
+
+
+def alu_roofline(model, units, kern_ms, peaks, n_sm):
+    """FP32 screen against the FP32 FMA lanes (SMs x 128 lanes x 2 flops x max clock)."""
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak = 2.0 * FP32_LANES_PER_SM * n_sm * sm_max * 1e6 / 1e12
+    ach = flops_per_sample_layer(model) * units / (kern_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "kernel_ms": kern_ms,
+            "work": f"{flops_per_sample_layer(model):.0f} flops per sample.layer (2d per candidate)",
+            "peak_basis": f"FP32 FMA lanes: {n_sm} SMs x {FP32_LANES_PER_SM} x 2 flops x {sm_max:.0f} MHz"}
+
+
+def timed_steps(ctx, step, K, W_, flush, stream, dist=None):
+    """W_ untimed steps, then K steps each between CUDA events on the launching stream
+    (a buffer larger than L2 written between steps, outside the events).  Returns
+    the mean step time, the library's per-step forward-region times and the stats."""
+    import torch
+    for _ in range(W_):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    kern = []
+    for i in range(K):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        kern.append(ctx.status()[1].ms)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return sum(ms) / K, kern, ctx.status()[1]
+
+
+def extra_workloads(ctx, B, dev, stream, flush, peaks, n_sm):
+    """Further workloads, each timed on its own (one replica, this GPU)."""
+    import torch
+    out = {}
+
+    def run(name, model, K, W_, o=None, pathwise=False):
+        g = bench_grids(ctx, B, model)
+        ct = counts_type_for(B, model, dev)
+        o = o or B.options(prec=model.prec, counts_type=ct)
+        o.counts_type = ct
+        counts = torch.empty(model.count_entries, dtype=torch.int64 if ct == B.COUNTS_I64 else torch.int32,
+                             device=dev)
+        f = ctx.transitions_pathwise if pathwise else ctx.transitions
+
+        def step():
+            f(model, g, model.M, model.seed, o, counts=counts, want_stats=False, stream=stream)
+        ms, kern, st = timed_steps(ctx, step, K, W_, flush, stream)
+        units = model.n * model.M
+        kmean = statistics.mean(kern) if kern and all(k > 0 for k in kern) else ms
+        r = {"workload": model.name, "d": model.d, "n": model.n, "N": int(model.N[-1]), "M": model.M,
+             "value": units / (ms / 1e3), "unit": "sample*layers/s", "ms_per_step": ms, "steps": K, "warmup": W_,
+             "form": "pathwise_f32" if pathwise else B.FORM_NAMES.get(st.form_used, "?"),
+             "counts": "int64" if ct == B.COUNTS_I64 else "uint32", "launches_per_step": st.launches,
+             "rechecks_per_step": st.rechecks}
+        if st.form_used == B.FORM_TC_RECHECK and not pathwise:
+            r["tc_draw"] = {1: "draw pass", 2: "in the screen kernel"}.get(st.tc_draw)
+            r["roofline"] = tensor_roofline(model, units, kmean, peaks)
+        else:
+            r["roofline"] = alu_roofline(model, units, kmean, peaks, n_sm)
+        del counts
+        torch.cuda.empty_cache()
+        return r, g
+
+    # the 10-d, 365-layer chain at full size (uint32 counts: 93 GB); one warm-up at M = 10^6
+    m5 = W.maxcall10()
+    _, _ = run("warm", W.maxcall10(M=10**6).restrict(n=4), 1, 1)
+    out["maxcall10_full"], _ = run("maxcall10", m5, 2, 0)
+    # the 4-d basket at full size
+    out["basket4_full"], _ = run("basket4", W.basket4(), 2, 1)
+    # the 2-factor OU workload: Algorithm III (FP32 screen) and Algorithm II (path-wise)
+    m2 = W.ou2()
+    out["ou2_alg3"], g2 = run("ou2", m2, 5, 3, B.options(form=B.FORM_F32_RECHECK, prec=m2.prec))
+    out["ou2_alg2_pathwise"], _ = run("ou2", m2, 5, 3, B.options(prec=m2.prec), pathwise=True)
+    out["ou2_alg2_pathwise"]["vs_alg3"] = out["ou2_alg2_pathwise"]["value"] / out["ou2_alg3"]["value"]
+    # the paper's scenario (d = 2, n = 365, M = 10^5, N = 500): Algorithm III and II
+    mp = W.paper(N=500)
+    out["paper_alg3"], _ = run("paper", mp, 5, 3, B.options(prec=mp.prec))
+    out["paper_alg2_pathwise"], _ = run("paper", mp, 5, 3, B.options(prec=mp.prec), pathwise=True)
+    # the swing option's backward induction on the 2-factor tree (100 dates, N = 500)
+    counts, _, _ = ctx.transitions(m2, g2, m2.M, m2.seed, B.options(prec=m2.prec), stream=stream)
+    v = torch.from_numpy(W.payoff_values(m2, g2.cpu().numpy()) - 0.004).to(dev)
+    sw = {}
+    for qmin, qmax in ((0, 1), (20, 60), (0, 100)):
+        ctx.swing(m2.N, counts, v, qmin, qmax, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P_, price = ctx.swing(m2.N, counts, v, qmin, qmax, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sw[f"Q[{qmin},{qmax}]"] = {"ms": e0.elapsed_time(e1), "price": price}
+    out["ou2_swing"] = sw
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -280,16 +412,14 @@ def main():
     ctx = B.Context(local)
     stream = torch.cuda.current_stream()
     seed = replica_seed(model, rank)          # independent replica per rank
-    grids = ctx.build_grids(model, grid_method(model), samples=max(20 * int(np.max(model.N)), 200000),
-                            iters=20, seed=W.GRID_SEED_BASE + W.CONFIG_INDEX[model.name])
+    grids = bench_grids(ctx, B, model)
     form = {"auto": B.FORM_AUTO, "plain_f64": B.FORM_PLAIN_F64, "f32_recheck": B.FORM_F32_RECHECK,
             "tc_recheck": B.FORM_TC_RECHECK, "router_cert": B.FORM_ROUTER_CERT}.get(args.form, B.FORM_AUTO)
     if form == B.FORM_AUTO:
         form = default_form(model, B)
     prec = model.prec
-    entries = int(np.sum(model.N[:-1] * model.N[1:]))
-    # int64 counts unless they would take more than a quarter of the device (then uint32)
-    ctype = B.COUNTS_I64 if entries * 8 <= torch.cuda.get_device_properties(dev).total_memory // 4 else B.COUNTS_U32
+    entries = model.count_entries
+    ctype = counts_type_for(B, model, dev)
     router = None
     router_info = None
     if form == B.FORM_ROUTER_CERT:
@@ -305,49 +435,21 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # larger than the 129 MB L2
     units = model.n * model.M
 
-    def step(o):
+    def step(o=opts):
         ctx.transitions(model, grids, model.M, seed, o, counts=counts, want_stats=False, stream=stream)
 
-    def timed(o, K, W_):
-        for _ in range(W_):
-            step(o)
-        torch.cuda.synchronize()
-        st = ctx.status()[1]
-        rech = st.rechecks
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        total, kern = 0.0, []
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        for i in range(K):
-            flush.fill_(i & 0xFF)                 # evict L2 between steps (outside the events)
-            ev[i][0].record(stream)
-            step(o)
-            ev[i][1].record(stream)
-            torch.cuda.synchronize()
-            kern.append(ctx.status()[1].ms)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        ms = [a.elapsed_time(b) for a, b in ev]
-        total = sum(ms)
-        return total / K, kern, rech
-
     with ClockSampler(local) as clk:
-        ms_step, kern_ms, rech = timed(opts, args.steps, max(3, args.warmup))
-    _st = ctx.status()[1]
-    cand = _st.candidates
-    diag = list(_st.diag)
+        ms_step, kern_ms, st = timed_steps(ctx, step, args.steps, max(3, args.warmup), flush, stream, dist)
     clocks = clk.summary()
     ms_step = max_over_ranks(ms_step, dist, dev) if dist else ms_step
     value = job_value(world, units, ms_step)
 
-    # plain GPU comparator (exact FP64 brute force for d <= 2)
+    # plain GPU comparator (exact FP64 brute force for d <= 2, FP32 screen otherwise)
     plain = None
     pform = plain_form(model, B)
     if args.plain_steps > 0 and pform != form:
         po = B.options(form=pform, prec=prec, counts_type=ctype)
-        pms, _, _ = timed(po, args.plain_steps, 1)
+        pms, _, _ = timed_steps(ctx, lambda: step(po), args.plain_steps, 1, flush, stream, dist)
         plain = {"form": B.FORM_NAMES[pform], "value": world * units / (pms / 1e3), "ms_per_step": pms}
 
     # end to end through the public API: host grids and payoff in, price out
@@ -358,7 +460,7 @@ def main():
     gpin = torch.from_numpy(gh).pin_memory()
     ppin = torch.from_numpy(phi).pin_memory()
     e2e_ms = []
-    for i in range(max(1, min(args.steps, 5)) + 1):
+    for i in range(max(1, min(args.steps, 3)) + 1):
         torch.cuda.synchronize()
         t = time.perf_counter()
         price, _ = ctx.price(model, gpin.numpy(), model.M, seed, ppin.numpy(), opts, stream=stream)
@@ -368,35 +470,26 @@ def main():
            "h2d_bytes_per_step": int(gh.nbytes + phi.nbytes), "d2h_bytes_per_step": 8,
            "ms_per_step": statistics.mean(e2e_ms), "price": price}
 
-    # roofline of the dominant kernel (the persistent forward kernel)
+    # roofline of the dominant kernel: the forward region (screen launches and, with
+    # the draw-pass layout, the draw passes), timed by the library's CUDA events on
+    # the launching stream at every timed step
     peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    props = torch.cuda.get_device_properties(dev)
-    n_sm = props.multi_processor_count
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     kmean = statistics.mean(kern_ms) if kern_ms and all(k > 0 for k in kern_ms) else ms_step
-    flops = flops_per_sample_layer(model) * units / world
-    peak = 2.0 * FP32_LANES_PER_SM * n_sm * sm_max * 1e6 / 1e12
+    if form == B.FORM_TC_RECHECK:
+        roofline = tensor_roofline(model, units, kmean, peaks)
+    else:
+        roofline = alu_roofline(model, units, kmean, peaks, n_sm)
     traffic = None
     if os.path.exists(TRAFFIC):
-        tj = json.load(open(TRAFFIC))
-        ent = tj.get(model.name)
+        ent = json.load(open(TRAFFIC)).get(model.name)
         if ent and ent.get("source_hash") == source_hash() and ent.get("form") == B.FORM_NAMES[form]:
             traffic = ent.get("bytes_per_launch")
-    achieved = flops / (kmean / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel_ms": kmean,
-                "peak_basis": f"FP32 FMA lanes: {n_sm} SMs x {FP32_LANES_PER_SM} x 2 flops x {sm_max:.0f} MHz"}
-    if form == B.FORM_TC_RECHECK:
-        # a contraction on the tensor cores: FP16 MMAs against the measured dense
-        # bf16 rate (the same rate as FP16 on this part), the sustained figure for
-        # a kernel timed inside a long step; the time spans the draw passes too
-        tpeak = peaks.get("bf16_tflops_sustained", 1700.0)
-        tach = tc_flops_per_sample_layer(model) * units / world / (kmean / 1e3) / 1e12
-        roofline = {"bound": "tensor", "achieved": tach, "peak": tpeak, "unit": "TFLOP/s", "frac": tach / tpeak,
-                    "traffic": traffic, "kernel_ms": kmean,
-                    "peak_basis": "measured dense bf16 GEMM, sustained (of measured)"
-                    if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)",
-                    "fp32_equivalent_tflops": achieved}
+    roofline["traffic"] = traffic
+
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = extra_workloads(ctx, B, dev, stream, flush, peaks, n_sm)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -410,16 +503,16 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": model.name, "d": model.d, "n": model.n, "N": int(model.N[-1]),
                            "M": model.M, "form": B.FORM_NAMES[form],
+                           "tc_draw": {1: "draw pass", 2: "in the screen kernel"}.get(st.tc_draw),
                            "counts": "int64" if ctype == B.COUNTS_I64 else "uint32",
                            "sample_prec": "f32" if prec == 1 else "f64",
                            "l2": "256 MiB buffer written between timed steps",
-                           "rechecks_per_step": rech,
-                           "uncertified_by_cause": diag if form == B.FORM_TC_RECHECK else None,
+                           "rechecks_per_step": st.rechecks,
+                           "uncertified_by_cause": list(st.diag) if form == B.FORM_TC_RECHECK else None,
                            "router": router_info,
-                           "candidates_per_search": (cand / (2 * units)) if router else None},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (tc_launches_per_step(model) if form == B.FORM_TC_RECHECK
-                                 else 3 if form == B.FORM_ROUTER_CERT else 2) * args.steps,
-                "clocks": clocks, "plain": plain}
+                           "candidates_per_search": (st.candidates / (2 * units)) if router else None},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": st.launches * args.steps, "clocks": clocks, "plain": plain, "extras": extras}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

@@ -129,10 +129,15 @@ typedef struct {
                               negative = give up at once (tests of the timeout path)       */
     const void* router;    /* qt_router* for QT_FORM_ROUTER_CERT, else NULL                */
     int32_t tile_samples_per_thread; /* 0 = autotuned                                       */
-    int32_t tc_chunk_items; /* tensor-core form: most work items (128 samples each) drawn per
-                              draw pass and screened per forward pass; 0 = as many as 2 GiB
-                              of drawn samples hold                                        */
-    int32_t reserved[2];
+    int32_t tc_chunk_items; /* tensor-core form: most work items (128 samples each) per kernel
+                              launch; 0 = the whole step in one launch (draw-pass layout:
+                              as many as 2 GiB of drawn samples hold)                      */
+    int32_t tc_draw;       /* tensor-core form: where the samples are drawn.  0 = autotuned
+                              (both timed once per dimension class), 1 = a separate draw
+                              pass writes them to device memory before each screen launch,
+                              2 = the screen kernel draws them itself (one launch, no
+                              device-memory hand-off)                                     */
+    int32_t reserved[1];
 } qt_options;
 
 /* Optional per-sample record: sample t of layer k is m = t * stride, t < count.
@@ -158,6 +163,10 @@ typedef struct {
     int64_t diag[3];        /* tensor-core form: uncertified picks by cause (FP32 bound
                                inside the re-scored chunks, tensor-core bound outside
                                them, index or FP16 range)                              */
+    int32_t launches;       /* kernels the forward step launched (preparation, draw
+                               passes, screens)                                        */
+    int32_t tc_draw;        /* tensor-core form: sample-draw layout run (1 = draw pass,
+                               2 = inside the screen kernel), else 0                   */
 } qt_stats;
 
 /* Context: one per device.  device = CUDA ordinal.  Not thread safe; use one

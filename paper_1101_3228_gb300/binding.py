@@ -44,7 +44,8 @@ class QtModel(ctypes.Structure):
 
 class QtOptions(ctypes.Structure):
     _fields_ = [("form", i32), ("sample_prec", i32), ("counts_type", i32), ("flags", u32),
-                ("spin_budget", i64), ("router", P), ("tile_samples_per_thread", i32), ("tc_chunk_items", i32), ("reserved", i32 * 2)]
+                ("spin_budget", i64), ("router", P), ("tile_samples_per_thread", i32), ("tc_chunk_items", i32), ("tc_draw", i32),
+                ("reserved", i32 * 1)]
 
 
 class QtDump(ctypes.Structure):
@@ -57,7 +58,8 @@ class QtEuler(ctypes.Structure):
 
 class QtStats(ctypes.Structure):
     _fields_ = [("samples", i64), ("rechecks", i64), ("searches", i64), ("candidates", i64),
-                ("form_used", i32), ("device_status", i32), ("ms", ctypes.c_double), ("diag", i64 * 3)]
+                ("form_used", i32), ("device_status", i32), ("ms", ctypes.c_double), ("diag", i64 * 3),
+                ("launches", i32), ("tc_draw", i32)]
 
 
 class QtRouterConfig(ctypes.Structure):
@@ -164,13 +166,14 @@ class HostModel:
 
 
 def options(form=FORM_AUTO, prec=PREC_F32, counts_type=COUNTS_I64, flags=0, spin_budget=0, router=None,
-            samples_per_thread=0, tc_chunk_items=0) -> QtOptions:
+            samples_per_thread=0, tc_chunk_items=0, tc_draw=0) -> QtOptions:
     o = QtOptions()
     o.form, o.sample_prec, o.counts_type, o.flags = form, prec, counts_type, flags
     o.spin_budget = spin_budget
     o.router = router
     o.tile_samples_per_thread = samples_per_thread
     o.tc_chunk_items = tc_chunk_items
+    o.tc_draw = tc_draw
     return o
 
 

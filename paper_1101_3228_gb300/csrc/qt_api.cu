@@ -81,6 +81,8 @@ struct qt_ctx {
     // autotuner cache: key -> samples per thread
     std::map<TuneKey, int> tune;
     int last_form = 0;
+    int last_launches = 0;             // kernels enqueued by the last forward step
+    int last_tc_draw = 0;              // sample-draw layout of the last tensor-core step
     void* status_buf = nullptr;   // status block of the last forward call
 };
 
@@ -309,7 +311,8 @@ struct Plan {
     int seg_records = 0;
     int tc_k = 0, tc_slots = 0, tc_resident = 0;
     long long tc_total_tiles = 0;
-    long long tc_chunk_items = 0;      // tensor-core form: work items per draw pass
+    long long tc_chunk_items = 0;      // tensor-core form: work items per launch
+    int tc_draw_in = 0;                // tensor-core form: 1 = the screen kernel draws its samples
     size_t tc_item_bytes = 0;          // tensor-core form: drawn-sample bytes per work item
     int d = 0, n = 0, ngrids = 0;
     int euler = 0;                     // path-wise form: Euler-scheme chain
@@ -337,11 +340,13 @@ struct FwdIO {
 qt_status make_plan_full(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, long long M,
                          const qt_options* o, bool from_arrays, Plan& P, int algo);
 
-// Work items per draw/forward pass of the tensor-core form: as many as 2 GiB of
-// drawn samples hold, or fewer when the caller caps it.
+// Work items per launch of the tensor-core form: all of them when the screen
+// kernel draws its own samples, as many as 2 GiB of drawn samples hold with the
+// draw pass, or fewer when the caller caps it.
 long long tc_chunk(const Plan& P, const qt_options* o)
 {
-    long long c = std::min<long long>(P.total_items, (2ll << 30) / (long long)P.tc_item_bytes);
+    long long c = P.total_items;
+    if (!P.tc_draw_in) c = std::min<long long>(c, (2ll << 30) / (long long)P.tc_item_bytes);
     if (o->tc_chunk_items > 0) c = std::min<long long>(c, o->tc_chunk_items);
     return std::max<long long>(1, c);
 }
@@ -446,7 +451,8 @@ qt_status make_plan_full(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
             return fail(ctx, QT_EUNSUPPORTED,
                         "the path-wise form keeps two grids in shared memory: %zu bytes exceed %zu", P.grid_bytes,
                         budget);
-        int S = o->tile_samples_per_thread > 0 ? o->tile_samples_per_thread : pathwise_default_spt(P.dm, f32);
+        int S = o->tile_samples_per_thread > 0 ? o->tile_samples_per_thread
+                                                : pathwise_default_spt(P.dm, f32, M, 2ll * ctx->num_sms);
         if (!pathwise_variant_exists(P.dm, S, f32))
             return fail(ctx, QT_EUNSUPPORTED, "no path-wise kernel for d %d, %d paths per thread", d, S);
         P.S = S;
@@ -528,9 +534,11 @@ qt_status make_plan_full(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
         P.S = 1;
         P.block = kTcThreads;
         P.tile = kTcTileM;
-        P.grid_bytes = (size_t)fixed + (size_t)P.tc_slots * tile_bytes;
-        // the draw pass writes the samples of up to 2 GiB worth of work items at a time
+        // where the samples are drawn: the caller's choice, else the autotuned
+        // one (the caller passes it through tc_draw), else in the screen kernel
+        P.tc_draw_in = o->tc_draw != 1;
         P.tc_item_bytes = (size_t)(tc_item_op_bytes(P.tc_k) + tc_item_cert_bytes(P.dm));
+        P.grid_bytes = (size_t)fixed + (size_t)P.tc_slots * tile_bytes;
         P.hist_bytes = 0;
         P.dyn_smem = P.grid_bytes;
         P.layers.resize(n);
@@ -730,20 +738,27 @@ qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long
         if (ce != cudaSuccess) return fail(ctx, QT_ECUDA, "grid checksum: %s", cudaGetErrorString(ce));
     }
     int blocks_per_sm = 0;
+    int launches = 1 + (P.form == kTcRecheck ? 1 : 0) + (P.form == kRouterCert ? 1 : 0);   // preparation
     // timing events around the kernel; inside a capture they must be external
     // event nodes to be recorded at every replay
     const unsigned evflags = stream_is_capturing(st) ? cudaEventRecordExternal : cudaEventRecordDefault;
     QT_CUDA(cudaEventRecordWithFlags(ctx->ev_k0, st, evflags));
     if (P.form == kTcRecheck) {
-        // draw pass and tensor-core pass, chunk by chunk of work items
+        // one launch over every work item (or one per window when capped); with
+        // the draw-pass layout each window's samples are drawn first
+        fp.tc_draw_in = P.tc_draw_in;
         fp.tc_items = (unsigned char*)dtcitems;
         for (long long lo = 0; lo < P.total_items; lo += P.tc_chunk_items) {
             fp.item_lo = lo;
             fp.item_hi = std::min(P.total_items, lo + P.tc_chunk_items);
-            cudaError_t e = launch_tc_draw(P.dm, fp, st);
-            if (e != cudaSuccess) return fail(ctx, QT_ECUDA, "draw pass launch: %s", cudaGetErrorString(e));
+            cudaError_t e = cudaSuccess;
+            if (!P.tc_draw_in) {
+                e = launch_tc_draw(P.dm, fp, st);
+                if (e != cudaSuccess) return fail(ctx, QT_ECUDA, "draw pass launch: %s", cudaGetErrorString(e));
+            }
             e = forward_launch(P.form, P.dm, P.S, P.streamed, fp, P.block, (int)P.dyn_smem, ctx->num_sms,
                                &blocks_per_sm, st);
+            launches += P.tc_draw_in ? 1 : 2;
             if (e != cudaSuccess) return fail(ctx, QT_ECUDA, "forward kernel launch: %s", cudaGetErrorString(e));
         }
     } else {
@@ -751,8 +766,11 @@ qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long
                                        &blocks_per_sm, st);
         if (e != cudaSuccess) return fail(ctx, QT_ECUDA, "forward kernel launch: %s", cudaGetErrorString(e));
     }
+    if (P.form != kTcRecheck) ++launches;
     QT_CUDA(cudaEventRecordWithFlags(ctx->ev_k1, st, evflags));
     ctx->timed = true;
+    ctx->last_launches = launches;
+    ctx->last_tc_draw = P.form == kTcRecheck ? (P.tc_draw_in ? 2 : 1) : 0;
     return QT_OK;
 }
 
@@ -769,6 +787,8 @@ qt_status read_status(qt_ctx* ctx, cudaStream_t st, qt_stats* stats, long long s
         stats->rechecks = (int64_t)hs.rechecks;
         stats->candidates = (int64_t)hs.candidates;
         stats->form_used = ctx->last_form;
+        stats->launches = ctx->last_launches;
+        stats->tc_draw = ctx->last_tc_draw;
         stats->device_status = hs.code;
         stats->ms = 0.0;
         for (int q = 0; q < 3; ++q) stats->diag[q] = (int64_t)hs.spare[q + 1] - (q == 0 ? 0 : 0);
@@ -813,7 +833,8 @@ qt_status run_plan(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long M, uns
     void* dtcitems = nullptr;
     if (P.form == kTcRecheck &&
         ((s = dev_get(ctx, (tag + "tctiles").c_str(), (size_t)P.tc_total_tiles * kTcTileN * P.tc_k * 2, &dtiles)) ||
-         (s = dev_get(ctx, (tag + "tcitems").c_str(), (size_t)P.tc_chunk_items * P.tc_item_bytes, &dtcitems))))
+         (!P.tc_draw_in &&
+          (s = dev_get(ctx, (tag + "tcitems").c_str(), (size_t)P.tc_chunk_items * P.tc_item_bytes, &dtcitems)))))
         return s;
     void *hlayers, *hgrids, *hpf, *hpd;
     if ((s = host_get(ctx, (tag + "layers").c_str(), sizeof(LayerDesc) * P.layers.size(), &hlayers))) return s;
@@ -949,6 +970,76 @@ qt_status autotune(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* m
     return QT_OK;
 }
 
+// Autotuner of the tensor-core form: time both sample-draw layouts (a separate
+// draw pass, or the screen kernel drawing its own samples) on the widest window
+// of up to four consecutive layer pairs with up to 2^20 samples each (best of
+// three runs), keep the faster for the key.
+qt_status autotune_tc(qt_ctx* ctx, int d, int n, const int64_t* Ns, const double* mus, const double* params_d_host,
+                      long long M, unsigned long long seed, const qt_options* o, int source, const FwdIO& io,
+                      const Plan& base, const TuneKey& key, cudaStream_t st)
+{
+    const int n2 = std::min(n, 4);
+    int k0 = 0;
+    long long wbest = -1;
+    for (int k = 0; k + n2 <= n; ++k) {
+        long long w = 0;
+        for (int q = k; q < k + n2; ++q) w += Ns[q] + Ns[q + 1];
+        if (w > wbest) {
+            wbest = w;
+            k0 = k;
+        }
+    }
+    Ns += k0;
+    mus += (long long)k0 * d;
+    if (params_d_host) params_d_host += (long long)k0 * base.pstride;
+    const long long M2 = std::min<long long>(M, 1ll << 20);
+    long long ent = 0;
+    for (int k = 0; k < n2; ++k) ent += Ns[k] * Ns[k + 1];
+    void* tcounts;
+    qt_status s = dev_get(ctx, "tune.counts", (size_t)ent * 8, &tcounts);
+    if (s) return s;
+    FwdIO tio = io;
+    tio.counts = tcounts;
+    tio.dump = nullptr;
+    tio.cellsA = tio.cellsB = nullptr;
+    cudaEvent_t e0, e1;
+    QT_CUDA(cudaEventCreate(&e0));
+    QT_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bestv = 2;
+    for (int v = 1; v <= 2; ++v) {
+        qt_options to = *o;
+        to.tc_draw = v;
+        to.tc_chunk_items = 0;
+        to.counts_type = QT_COUNTS_I64;
+        to.flags |= QT_FLAG_NO_TUNE;
+        Plan P;
+        if (make_plan(ctx, d, n2, Ns, mus, M2, &to, source == kArrays, P) != QT_OK) continue;
+        float fastest = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            QT_CUDA(cudaEventRecord(e0, st));
+            if ((s = run_plan(ctx, P, tio, M2, seed, &to, source, params_d_host, st, false, "tune."))) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return s;
+            }
+            QT_CUDA(cudaEventRecord(e1, st));
+            QT_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            QT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) fastest = std::min(fastest, ms);     // the first run warms up
+        }
+        if (fastest < best) {
+            best = fastest;
+            bestv = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tune[key] = bestv;
+    return QT_OK;
+}
+
 TuneKey tune_key(const Plan& P, int prec, const int64_t* Ns, int n)
 {
     long long mx = 1;
@@ -974,6 +1065,22 @@ qt_status forward_common(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
     if (s) return s;
     P.euler = euler;
     const bool capturing = stream_is_capturing(st);
+    if (P.form == kTcRecheck && o->tc_draw == 0 && !(o->flags & QT_FLAG_NO_TUNE) && !capturing &&
+        o->spin_budget >= 0 && source == kSampler) {
+        const TuneKey key = tune_key(P, o->sample_prec, Ns, n);
+        if (!ctx->tune.count(key)) {
+            if ((s = autotune_tc(ctx, d, n, Ns, mus, params_d_host, M, seed, o, source, io, P, key, st))) return s;
+        }
+        if (o != &oi) {
+            oi = *o;
+            o = &oi;
+        }
+        oi.tc_draw = ctx->tune[key];
+        Plan P2;
+        if ((s = make_plan(ctx, d, n, Ns, mus, M, o, source == kArrays, P2, only_layer, algo))) return s;
+        P2.euler = euler;
+        P = P2;
+    }
     if (P.form != kTcRecheck && P.form != kRouterCert && P.form != kPathwise && o->tile_samples_per_thread <= 0 &&
         !(o->flags & QT_FLAG_NO_TUNE) && !capturing && o->spin_budget >= 0) {
         const TuneKey key = tune_key(P, source == kArrays ? 0 : o->sample_prec, Ns, n);
@@ -1209,8 +1316,12 @@ extern "C" qt_status qt_swing(qt_ctx* ctx, int32_t n, const int64_t* N, const vo
     swing_terminal_kernel<<<(unsigned)((tn + 255) / 256), 256, 0, st>>>((int)N[n], n, Qmin, Qmax, P + nq * goff[n]);
     QT_CUDA(cudaGetLastError());
     const int u32 = counts_type == QT_COUNTS_U32;
+    const long long qchunks = (Qmax + kSwingQ) / kSwingQ;   // warps per grid row
+    for (int k = 0; k < n; ++k)
+        if ((N[k] * qchunks * 32 + 255) / 256 > 0x7FFFFFFFll)
+            return fail(ctx, QT_EINVAL, "N[%d] x (Qmax + 1) too large for one launch", k);
     for (int k = n - 1; k >= 0; --k) {
-        const long long threads = (long long)N[k] * 32;
+        const long long threads = (long long)N[k] * qchunks * 32;
         swing_layer_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
             counts, u32, coff[k], (int)N[k], (int)N[k + 1], v + goff[k], P + nq * goff[k + 1], P + nq * goff[k], n,
             k, Qmin, Qmax);

@@ -54,13 +54,14 @@ struct GridInfo {
 
 constexpr int kTcTileN = 256;      // grid points per tensor-core operand tile (MMA N)
 constexpr int kTcTileM = 128;      // samples per tensor-core work item (MMA M)
-constexpr int kTcThreads = 512;    // tensor-core form: 16 warps (8 epilogue, 2 MMA, 2 loaders, 4 certifier)
+constexpr int kTcThreads = 512;    // tensor-core form: 16 warps (8 epilogue, 2 MMA, tile loader, draw, 4 certifier)
 constexpr int kTcMaxSlots = 16;    // tensor-core form: most operand tiles held in shared memory
 
-// Bytes of one work item's drawn samples in the tensor-core form, as the draw
-// pass writes them and the forward kernel copies them: the FP16 operand rows
-// of both grids (128 x K each, core-matrix layout), then the centred FP32
-// coordinates and norms ([grid][dm + 1][128]).
+// Bytes of one work item's drawn samples in the tensor-core form, as the
+// certifier warps draw them into an item slot in shared memory, or the draw
+// pass writes them to device memory: the FP16 operand rows of both grids
+// (128 x K each, core-matrix layout), then the centred FP32 coordinates and
+// norms ([grid][dm + 1][128]).
 __host__ __device__ constexpr long long tc_item_op_bytes(int K) { return 2ll * kTcTileM * K * 2; }
 __host__ __device__ constexpr long long tc_item_cert_bytes(int dm) { return 2ll * (dm + 1) * kTcTileM * 4; }
 
@@ -119,7 +120,8 @@ struct ForwardParams {
     int32_t tc_slots;              // ring slots of operand tiles in shared memory
     int32_t tc_resident;           // 1: both grids' tiles stay in shared memory for the layer
     long long item_lo, item_hi;    // tensor-core form: work items [item_lo, item_hi) of this launch
-    unsigned char* tc_items;       // tensor-core form: drawn samples of those items, tc_item_*_bytes each
+    int32_t tc_draw_in;            // tensor-core form: 1 = the screen kernel draws its samples
+    unsigned char* tc_items;       // tensor-core form, draw pass: samples of the launch's items
     // learned router + Elkan certificate
     const float* rt_params;        // MLP parameters, packed W1, b1, W2, b2, W3, b3
     const float* rt_linv;          // [n+1][d][d] FP32 inverse Cholesky factors (whitening)
@@ -131,6 +133,8 @@ struct ForwardParams {
     int32_t rt_N;                  // common grid size of layers >= 1
     unsigned long long rt_checksum;// checksum of the grids the router was built for
 };
+
+constexpr int kSwingQ = 8;         // swing option: consumption states per warp
 
 constexpr int kRtHidden = 64;      // router MLP width
 constexpr int kRtBuckets = 64;     // router classes (buckets of grid points)

@@ -119,10 +119,11 @@ __global__ void backward_layer_kernel(const void* __restrict__ counts, int u32, 
 //   P_k(i, Q) = max over admissible x of x v_k(i) + C_k(i, Q + x),
 //   C_k(i, Q') = (sum_j p^k_ij P_{k+1}(j, Q')) / p^k_i   (0 for an empty row),
 // -inf where no x is admissible.  P blocks are Q-major: [Qmax + 1][N].  One
-// warp per row i walks Q upwards and carries C(i, Q + 1) to the next Q, so each
-// continuation is summed once, in the order of backward_layer_kernel (lanes
-// j mod 32 ascending, then the fixed butterfly), which makes the one-right
-// swing (Qmax = 1) the Bermudan of qt_backward bit for bit.
+// warp per (row i, chunk of kSwingQ consumption states) walks its Q upwards and
+// carries C(i, Q + 1) to the next Q; every continuation is summed by one warp
+// in the order of backward_layer_kernel (lanes j mod 32 ascending, then the
+// fixed butterfly), whichever warp it is, which makes the one-right swing
+// (Qmax = 1) the Bermudan of qt_backward bit for bit.
 __device__ __forceinline__ bool swing_feasible(int n, int k, int Q, int Qmin, int Qmax)
 {
     return Q <= Qmax && Q + (n - k) >= Qmin;
@@ -140,9 +141,12 @@ __global__ void swing_layer_kernel(const void* __restrict__ counts, int u32, lon
                                    const double* __restrict__ vk, const double* __restrict__ Pnext,
                                    double* __restrict__ Pk, int n, int k, int Qmin, int Qmax)
 {
-    const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= Nk) return;
+    const int qchunks = (Qmax + kSwingQ) / kSwingQ;
+    if (gw >= (long long)Nk * qchunks) return;
+    const int warp = (int)(gw / qchunks);              // grid row i
+    const int q0 = (int)(gw % qchunks) * kSwingQ;      // first consumption state of this warp
     const long long row = coff + (long long)warp * Nk1;
     const uint32_t* c32 = reinterpret_cast<const uint32_t*>(counts) + row;
     const long long* c64 = reinterpret_cast<const long long*>(counts) + row;
@@ -165,8 +169,9 @@ __global__ void swing_layer_kernel(const void* __restrict__ counts, int u32, lon
         return ci == 0 ? 0.0 : __ddiv_rn(acc, (double)ci);
     };
     const double v = vk[warp];
-    double c_cur = cont(0);
-    for (int Q = 0; Q <= Qmax; ++Q) {
+    double c_cur = cont(q0);
+    const int q1 = min(Qmax, q0 + kSwingQ - 1);
+    for (int Q = q0; Q <= q1; ++Q) {
         const double c_next = Q + 1 <= Qmax ? cont(Q + 1) : ninf;
         double best = ninf;
         if (swing_feasible(n, k + 1, Q, Qmin, Qmax)) best = c_cur;                  // x = 0

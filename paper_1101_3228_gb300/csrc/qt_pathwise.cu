@@ -451,8 +451,9 @@ static cudaError_t launch_pw(const ForwardParams& p, int dyn, int num_sms, int* 
 
 // Compiled (dimension class, paths per thread) pairs: FP32 samples for every
 // class, FP64 samples for the small classes (the 1-d FP64 workload and tests).
-static const int kPwF32[][2] = {{1, 8}, {2, 8}, {2, 4}, {3, 4}, {4, 4}, {6, 2}, {8, 2}, {10, 2}, {12, 1}, {16, 1}};
-static const int kPwF64[][2] = {{1, 4}, {2, 4}, {4, 2}, {8, 1}};
+static const int kPwF32[][2] = {{1, 8}, {1, 2}, {2, 8}, {2, 4}, {2, 2}, {2, 1}, {3, 4}, {4, 4}, {4, 1},
+                                {6, 2}, {8, 2}, {8, 1}, {10, 2}, {10, 1}, {12, 1}, {16, 1}};
+static const int kPwF64[][2] = {{1, 4}, {1, 1}, {2, 4}, {2, 1}, {4, 2}, {8, 1}};
 
 bool pathwise_variant_exists(int dm, int S, bool f32)
 {
@@ -466,10 +467,18 @@ bool pathwise_variant_exists(int dm, int S, bool f32)
     return false;
 }
 
-int pathwise_default_spt(int dm, bool f32)
+// Paths per thread: the register-budget choice, lowered while the path tiles
+// would not give every CTA slot (ctas = SMs x resident CTAs) about two tiles --
+// the path-wise form has only M paths of parallelism.
+int pathwise_default_spt(int dm, bool f32, long long M, long long ctas)
 {
-    if (f32) return dm <= 2 ? 8 : (dm <= 4 ? 4 : (dm <= 10 ? 2 : 1));
-    return dm <= 2 ? 4 : (dm <= 4 ? 2 : 1);
+    int S = f32 ? (dm <= 2 ? 8 : (dm <= 4 ? 4 : (dm <= 10 ? 2 : 1))) : (dm <= 2 ? 4 : (dm <= 4 ? 2 : 1));
+    while (S > 1) {
+        const int next = S / 2;
+        if (M >= 2ll * ctas * 256 * S || !pathwise_variant_exists(dm, next, f32)) break;
+        S = next;
+    }
+    return S;
 }
 
 cudaError_t launch_pathwise(int dm, int S, bool f32, const ForwardParams& p, int dyn, int num_sms, int* bps,
@@ -477,9 +486,12 @@ cudaError_t launch_pathwise(int dm, int S, bool f32, const ForwardParams& p, int
 {
 #define QT_CASE(D, SS, F) \
     if (dm == D && S == SS && f32 == F) return launch_pw<D, SS, F>(p, dyn, num_sms, bps, st);
-    QT_CASE(1, 8, true) QT_CASE(2, 8, true) QT_CASE(2, 4, true) QT_CASE(3, 4, true) QT_CASE(4, 4, true)
-    QT_CASE(6, 2, true) QT_CASE(8, 2, true) QT_CASE(10, 2, true) QT_CASE(12, 1, true) QT_CASE(16, 1, true)
-    QT_CASE(1, 4, false) QT_CASE(2, 4, false) QT_CASE(4, 2, false) QT_CASE(8, 1, false)
+    QT_CASE(1, 8, true) QT_CASE(1, 2, true) QT_CASE(2, 8, true) QT_CASE(2, 4, true) QT_CASE(2, 2, true)
+    QT_CASE(2, 1, true) QT_CASE(3, 4, true) QT_CASE(4, 4, true) QT_CASE(4, 1, true) QT_CASE(6, 2, true)
+    QT_CASE(8, 2, true) QT_CASE(8, 1, true) QT_CASE(10, 2, true) QT_CASE(10, 1, true) QT_CASE(12, 1, true)
+    QT_CASE(16, 1, true)
+    QT_CASE(1, 4, false) QT_CASE(1, 1, false) QT_CASE(2, 4, false) QT_CASE(2, 1, false) QT_CASE(4, 2, false)
+    QT_CASE(8, 1, false)
 #undef QT_CASE
     return cudaErrorInvalidValue;
 }

@@ -71,26 +71,28 @@ def test_full_grid_sizes_bit_exact(ctx, B, name, n, M, ctype):
     _compare(B, model, counts, ref)
 
 
+@pytest.mark.parametrize("draw", [1, 2], ids=["draw-pass", "draw-in-kernel"])
 @pytest.mark.parametrize("name,n,N,M,chunk", [
     ("basket4", 50, 0, 4999, 7),          # uneven N_k up to 2000, resident operand tiles
     ("ar8", 3, 4000, 40111, 29),         # streamed operand-tile ring
     ("maxcall10", 2, 8000, 9001, 40),    # streamed ring, K = 32
 ])
-def test_tensor_core_many_passes_bit_exact(ctx, B, name, n, N, M, chunk):
-    """The draw/forward chunk loop: several passes over a reused sample buffer, each
-    with its own window of work items, the last one ragged, counts accumulated."""
+def test_tensor_core_many_passes_bit_exact(ctx, B, name, n, N, M, chunk, draw):
+    """Several launches, each over its own window of work items, the last one ragged,
+    counts accumulated: with the draw pass (a reused sample buffer in device memory)
+    and with the screen kernel drawing its own samples."""
     full = W.get(name, M=M)
     model = full.restrict(n=n, N=N) if N else full.restrict(n=n)
     g = _bench_grids(ctx, B, model)
     items = model.n * ((model.M + 127) // 128)
     assert items // chunk >= 3 and items % chunk != 0
     counts, stats, _ = ctx.transitions(model, g, model.M, model.seed,
-                                       B.options(form=B.FORM_TC_RECHECK, tc_chunk_items=chunk))
+                                       B.options(form=B.FORM_TC_RECHECK, tc_chunk_items=chunk, tc_draw=draw))
     assert stats.device_status == 0 and stats.form_used == B.FORM_TC_RECHECK
     ref = oracle.transitions(model, g.cpu().numpy(), model.M, model.seed, oracle.PREC_F32)
     _compare(B, model, counts, ref)
-    # the same counts as a single pass
-    one, _, _ = ctx.transitions(model, g, model.M, model.seed, B.options(form=B.FORM_TC_RECHECK))
+    # the same counts in one launch, in the other layout
+    one, _, _ = ctx.transitions(model, g, model.M, model.seed, B.options(form=B.FORM_TC_RECHECK, tc_draw=3 - draw))
     assert torch.equal(one, counts)
 
 

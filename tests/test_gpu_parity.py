@@ -132,14 +132,17 @@ TC_CASES = [("ou2", 500, 20011, 6), ("basket4", 0, 9001, 3), ("ar8", 700, 5003, 
             ("maxcall10", 500, 3001, 2), ("maxcall10", 8000, 2003, 2)]
 
 
+@pytest.mark.parametrize("draw", [1, 2], ids=["draw-pass", "draw-in-kernel"])
 @pytest.mark.parametrize("name,N,M,n", TC_CASES)
-def test_counts_bit_exact_tensor_core(ctx, B, name, N, M, n):
+def test_counts_bit_exact_tensor_core(ctx, B, name, N, M, n, draw):
     """tcgen05 screen: resident operand tiles (N <= a few thousand) and the
-    streamed ring (d = 8, N = 4000; d = 10, N = 8000), against the oracle."""
+    streamed ring (d = 8, N = 4000; d = 10, N = 8000), against the oracle, with
+    both sample-draw layouts."""
     model = _model(name, M=M, n=n, N=N) if N else _model(name, M=M, n=n)
     g = W.layer_grids(model, samples=max(20000, 3 * int(model.N[-1])), iters=3) if model.grid_kind == "kmeans" \
         else W.layer_grids(model)
-    counts, stats, _ = ctx.transitions(model, _dev(g), model.M, model.seed, B.options(form=B.FORM_TC_RECHECK))
+    counts, stats, _ = ctx.transitions(model, _dev(g), model.M, model.seed,
+                                       B.options(form=B.FORM_TC_RECHECK, tc_draw=draw))
     ref = oracle.transitions(model, g, model.M, model.seed, oracle.PREC_F32)
     got = B.split_counts(model.N, counts.cpu().numpy())
     for k in range(model.n):
@@ -219,11 +222,13 @@ def test_tensor_core_fp64_samples_and_u32_counts(ctx, B):
     assert stats.form_used == B.FORM_TC_RECHECK and stats.device_status == 0
 
 
-def test_tensor_core_timeout_is_reported(ctx, B):
+@pytest.mark.parametrize("draw", [1, 2], ids=["draw-pass", "draw-in-kernel"])
+def test_tensor_core_timeout_is_reported(ctx, B, draw):
     model = _model("ar8", M=600, n=2, N=4000)
     g = _dev(W.layer_grids(model, samples=12000, iters=2))
     with pytest.raises(B.QtError) as e:
-        ctx.transitions(model, g, model.M, model.seed, B.options(form=B.FORM_TC_RECHECK, spin_budget=-1))
+        ctx.transitions(model, g, model.M, model.seed, B.options(form=B.FORM_TC_RECHECK, spin_budget=-1,
+                                                                 tc_draw=draw))
     assert e.value.status == B.QT_ETIMEOUT
     counts, _, _ = ctx.transitions(model, g, model.M, model.seed, B.options(form=B.FORM_TC_RECHECK))
     assert int(counts.sum()) == model.n * model.M
