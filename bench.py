@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--M", type=int, default=0, help="override samples per layer")
+    ap.add_argument("--layers", type=int, default=0, help="first n layers only (small profiling cases)")
     ap.add_argument("--spt", type=int, default=0, help="samples per thread (0 = library choice)")
     ap.add_argument("--router-samples", type=int, default=10**7, help="labelled pairs for the router form")
     return ap.parse_args()
@@ -393,6 +394,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     model = workload(args.config, args.M)
+    if args.layers:
+        model = model.restrict(n=min(args.layers, model.n))
     if args.impl == "reference":
         run_reference(args, model, rank, world)
         return
@@ -480,10 +483,14 @@ def main():
         roofline = tensor_roofline(model, units, kmean, peaks)
     else:
         roofline = alu_roofline(model, units, kmean, peaks, n_sm)
+    layout = {1: "draw pass", 2: "in the screen kernel"}.get(st.tc_draw)
     traffic = None
     if os.path.exists(TRAFFIC):
+        # DRAM bytes of one ncu capture of this kernel, kept only while the sources,
+        # the form and the sample-draw layout are those it was taken on
         ent = json.load(open(TRAFFIC)).get(model.name)
-        if ent and ent.get("source_hash") == source_hash() and ent.get("form") == B.FORM_NAMES[form]:
+        if ent and ent.get("source_hash") == source_hash() and ent.get("form") == B.FORM_NAMES[form] and \
+                ent.get("layout") == layout and model.M == W.get(model.name).M and model.n == W.get(model.name).n:
             traffic = ent.get("bytes_per_launch")
     roofline["traffic"] = traffic
 
@@ -503,7 +510,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": model.name, "d": model.d, "n": model.n, "N": int(model.N[-1]),
                            "M": model.M, "form": B.FORM_NAMES[form],
-                           "tc_draw": {1: "draw pass", 2: "in the screen kernel"}.get(st.tc_draw),
+                           "tc_draw": layout,
                            "counts": "int64" if ctype == B.COUNTS_I64 else "uint32",
                            "sample_prec": "f32" if prec == 1 else "f64",
                            "l2": "256 MiB buffer written between timed steps",
