@@ -125,8 +125,9 @@ typedef struct {
     int32_t sample_prec;   /* QT_PREC_*                                                    */
     int32_t counts_type;   /* QT_COUNTS_* (element type of the counts array)               */
     uint32_t flags;        /* QT_FLAG_*                                                    */
-    int64_t spin_budget;   /* iterations of every bounded device wait; 0 = library default;
-                              negative = give up at once (tests of the timeout path)       */
+    int64_t spin_budget;   /* bound of every device wait, in microseconds of the GPU's global
+                              timer; 0 = library default (10 s); negative = give up at once
+                              (tests of the timeout path)                                  */
     const void* router;    /* qt_router* for QT_FORM_ROUTER_CERT, else NULL                */
     int32_t tile_samples_per_thread; /* 0 = autotuned                                       */
     int32_t tc_chunk_items; /* tensor-core form: most work items (128 samples each) per kernel

@@ -706,7 +706,7 @@ qt_status enqueue_forward(qt_ctx* ctx, const Plan& P, const FwdIO& io, long long
     fp.smem_grid_bytes = (int)P.grid_bytes;
     fp.smem_hist_entries = (int)(P.hist_bytes / 4);
     fp.seg_records = P.seg_records;
-    fp.spin_budget = o->spin_budget == 0 ? (1ll << 26) : o->spin_budget;
+    fp.spin_budget = o->spin_budget == 0 ? 10000000ll : o->spin_budget;   // microseconds (10 s default)
     fp.pathwise_euler = P.euler;
     fp.layers = (const LayerDesc*)dlayers;
     fp.grids = (const GridInfo*)dgrids;

@@ -68,12 +68,15 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  : "memory");
 }
 
+// One wait on the phase `parity` of an mbarrier: the thread may be suspended
+// in hardware until the phase completes, for at most about 20 microseconds
+// (the suspend-time hint), so waiting warps take few issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 20000;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(bar), "r"(parity)
@@ -81,14 +84,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: at most `budget` polls; budget < 0 gives up without polling.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long budget)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    if (budget < 0) return false;
-    for (long long it = 0; it <= budget; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
+
+// Bounded wait: gives up once `budget_us` microseconds of the global timer have
+// passed; budget_us < 0 gives up without waiting.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long budget_us)
+{
+    if (budget_us < 0) return false;
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    const unsigned long long lim = (unsigned long long)budget_us * 1000ull;
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > lim) return false;
+    }
+}
+
+// Bound of the waits that drain a CTA's own copies before it leaves (after a
+// timeout elsewhere): 20 s.
+constexpr long long kDrainUs = 20000000;
 
 __device__ __forceinline__ float min3f(float a, float b, float c)
 {
@@ -693,7 +712,7 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) forward_kernel(const F
                     record_error(p.status, 4 /* QT_ETIMEOUT */, 1);
                     s_abort = 1;
                 }
-                mbar_wait_bounded(bar, phase, 1ll << 24);
+                mbar_wait_bounded(bar, phase, kDrainUs);
             }
             if (resident) phase ^= 1u;
             __syncthreads();
@@ -802,7 +821,7 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) forward_kernel(const F
                         record_error(p.status, 4 /* QT_ETIMEOUT */, 3);
                         s_abort = 1;
                     }
-                    if (!ok) mbar_wait_bounded(smem_u32(&s_ring_bar[slot]), ring_phase[slot], 1ll << 24);
+                    if (!ok) mbar_wait_bounded(smem_u32(&s_ring_bar[slot]), ring_phase[slot], kDrainUs);
                     ring_phase[slot] ^= 1u;
                     pending[slot] = false;
                     const bool isA = t < nA;
@@ -853,7 +872,7 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) forward_kernel(const F
                     // let the copies still in flight land before the CTA leaves
 #pragma unroll
                     for (int t = 0; t < kSlots; ++t)
-                        if (pending[t]) mbar_wait_bounded(smem_u32(&s_ring_bar[t]), ring_phase[t], 1ll << 24);
+                        if (pending[t]) mbar_wait_bounded(smem_u32(&s_ring_bar[t]), ring_phase[t], kDrainUs);
                     break;
                 }
             }

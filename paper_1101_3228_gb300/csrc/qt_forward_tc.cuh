@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
             }
             // every MMA issued completes before the tensor memory is released
             tc_commit(smem_u32(&s_drain[ib]));
-            mbar_wait_bounded(smem_u32(&s_drain[ib]), 0u, 1ll << 24);
+            mbar_wait_bounded(smem_u32(&s_drain[ib]), 0u, kDrainUs);
         }
     } else if (warp == kLoadWarp) {
         // ================================================================ operand tiles
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                     ++layers;
                 }
                 // the last layer's copies land before the shared memory is released
-                for (int i = 0; i < lastT; ++i) mbar_wait_bounded(smem_u32(&s_tfull[i]), (tph >> i) & 1u, 1ll << 24);
+                for (int i = 0; i < lastT; ++i) mbar_wait_bounded(smem_u32(&s_tfull[i]), (tph >> i) & 1u, kDrainUs);
             } else {
                 // the tiles of every item in order, through the ring
                 long long ql = 0, ln = 0;
@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                         r = RS - 1;
                         rph ^= 1u;
                     }
-                    mbar_wait_bounded(smem_u32(&s_tfull[r]), rph, 1ll << 24);
+                    mbar_wait_bounded(smem_u32(&s_tfull[r]), rph, kDrainUs);
                 }
             }
         }
@@ -611,18 +611,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                 const int acc = 2 * wg + h;
                 if (!warp_wait(smem_u32(&s_accfull[acc]), (uint32_t)((gg >> 1) & 1), p.spin_budget)) return false;
                 tc_fence_after();
+                // all chunk minima of the half first, so that the accumulator goes
+                // back to the MMA warp before the tracking work
+                float mc[kHalfN / kChunk];
 #pragma unroll
-                for (int q = 0; q < kHalfN / 64; ++q) {
-                    float m0, m1, m2, m3;
-                    tc_chunk_min4(trow + (uint32_t)(acc * kHalfN + q * 64), m0, m1, m2, m3);
-                    const int c0 = lt * (kTcTileN / kChunk) + h * (kHalfN / kChunk) + q * 4;
-                    tr.add(m0, c0);
-                    tr.add(m1, c0 + 1);
-                    tr.add(m2, c0 + 2);
-                    tr.add(m3, c0 + 3);
-                }
+                for (int q = 0; q < kHalfN / 64; ++q)
+                    tc_chunk_min4(trow + (uint32_t)(acc * kHalfN + q * 64), mc[4 * q], mc[4 * q + 1], mc[4 * q + 2],
+                                  mc[4 * q + 3]);
                 tc_fence_before();
                 mbar_arrive(smem_u32(&s_accempty[acc]));
+                const int c0 = lt * (kTcTileN / kChunk) + h * (kHalfN / kChunk);
+#pragma unroll
+                for (int q = 0; q < kHalfN / kChunk; ++q) tr.add(mc[q], c0 + q);
             }
             return true;
         };
@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                 }
                 // the copies of the last two items land before the shared memory is released
                 for (long long q = n > 2 ? n - 2 : 0; q < n; ++q)
-                    mbar_wait_bounded(smem_u32(&s_opfull[q & 1]), (uint32_t)((q >> 1) & 1), 1ll << 24);
+                    mbar_wait_bounded(smem_u32(&s_opfull[q & 1]), (uint32_t)((q >> 1) & 1), kDrainUs);
             }
         }
     } else if (warp >= kCertWarp0) {
@@ -780,15 +780,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
             need = valid && !cert;
             return c.idx;
         };
-        // exact window search of the lanes in `need` (the whole warp takes part)
-        auto recheck = [&](int s, int gr, const SlotLayer& S, unsigned long long ms, bool need, int& cell) {
+        // exact window search of the lanes in `need` (the whole warp takes part),
+        // from the centred sample the first pass copied out of the item slot
+        auto recheck = [&](const Pass& c, int gr, const SlotLayer& S, unsigned long long ms, bool need, int& cell) {
             unsigned mask = __ballot_sync(0xFFFFFFFFu, need);
             if (!mask) return;
-            const float* cx = scert + (s * 2 + gr) * (DM + 1) * kTcTileM + t;
-            float xs[DM];
-#pragma unroll
-            for (int l = 0; l < DM; ++l) xs[l] = cx[l * kTcTileM];
-            const float A = fabsf(cx[DM * kTcTileM]);
+            const float A = c.A;
             const int k = S.k;
             const float* gpf = p.params_f ? p.params_f + (long long)k * p.params_stride : nullptr;
             const double* gpd = p.params_d ? p.params_d + (long long)k * p.params_stride : nullptr;
@@ -801,7 +798,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                 mask &= mask - 1;
                 double z[DM];
                 if (lane == src) exact_sample<DM>(p, gpf, gpd, k, ms, gr == 1, z);
-                const int r = warp_window_nn<DM>(xs, A, z, src, recs, Npad, g64, Nown, d);
+                const int r = warp_window_nn<DM>(c.x, A, z, src, recs, Npad, g64, Nown, d);
                 if (lane == src) cell = r;
                 if (lane == 0) atomicAdd(&p.status->rechecks, 1ull);
             }
@@ -884,13 +881,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
             Pass pa, pb;
             first(s, 0, S, pa);
             first(s, 1, S, pb);
+            // the chunk states and the item slot are read (the passes hold copies):
+            // release them at once, so that the epilogue and the next item can move in
             mbar_arrive(smem_u32(&s_stempty[s]));
+            if constexpr (!DRAW_IN) mbar_arrive(smem_u32(&s_certdone[s]));   // the draw pass may refill the slot
             int ci = finish(pa, S.NA, valid, needA);
             int cj = finish(pb, S.NB, valid, needB);
-            recheck(s, 0, S, ms, needA, ci);
-            recheck(s, 1, S, ms, needB, cj);
+            recheck(pa, 0, S, ms, needA, ci);
+            recheck(pb, 1, S, ms, needB, cj);
             if constexpr (DRAW_IN) {
-                // item n + 2 into this slot, once the MMAs of item n are complete
+                // item n + 2 into this slot, once item n is certified and its MMAs are
+                // complete (drawing before the recheck keeps both passes' registers
+                // live across the draw and spills more)
                 if (p.item_lo + blockIdx.x + (n + 2) * G < p.item_hi) {
                     if (!warp_wait(smem_u32(&s_opempty[s]), (uint32_t)((n >> 1) & 1), p.spin_budget)) {
                         fail(31);
@@ -898,8 +900,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                     }
                     draw(n + 2);
                 }
-            } else {
-                mbar_arrive(smem_u32(&s_certdone[s]));
             }
             // ---- counters p^k_ij
             if (valid) {

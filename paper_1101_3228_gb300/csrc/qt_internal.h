@@ -90,7 +90,7 @@ struct ForwardParams {
     int32_t smem_grid_bytes;       // bytes of dynamic smem reserved for grids
     int32_t smem_hist_entries;     // u32 entries reserved for the private histogram
     int32_t seg_records;           // streamed mode: records per ring slot (multiple of kChunk)
-    long long spin_budget;         // bounded waits; < 0: give up at once
+    long long spin_budget;         // bound of every device wait in microseconds; < 0: give up at once
     int32_t pathwise_euler;        // Algorithm II: 1 = Euler-scheme chain (innovation rows scaled)
     // tables
     const LayerDesc* layers;

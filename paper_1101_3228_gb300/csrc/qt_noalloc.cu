@@ -190,7 +190,7 @@ extern "C" qt_status qt_counts_from_samples_noalloc(int32_t d, const double* gA,
     fp.rec64_doubles = 2;
     fp.smem_grid_bytes = (int)grid_bytes;
     fp.smem_hist_entries = 0;
-    fp.spin_budget = 1ll << 26;
+    fp.spin_budget = 10000000ll;   // microseconds
     fp.layers = dlayer;
     fp.grids = dgrids;
     fp.g64 = dg64;

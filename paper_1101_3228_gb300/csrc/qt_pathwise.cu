@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const 
         if (!mbar_wait_bounded(smem_u32(&s_bar[b]), phase[b], p.spin_budget)) {
             record_error(p.status, 4 /* QT_ETIMEOUT */, 40);
             s_abort = 1;
-            mbar_wait_bounded(smem_u32(&s_bar[b]), phase[b], 1ll << 24);
+            mbar_wait_bounded(smem_u32(&s_bar[b]), phase[b], kDrainUs);
         }
         phase[b] ^= 1u;
         pending[b] = false;
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const 
         if (aborted) {
             // let the copies still in flight land before the CTA leaves
             for (int b = 0; b < 2; ++b)
-                if (pending[b]) mbar_wait_bounded(smem_u32(&s_bar[b]), phase[b], 1ll << 24);
+                if (pending[b]) mbar_wait_bounded(smem_u32(&s_bar[b]), phase[b], kDrainUs);
             break;
         }
     }
