@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--M", type=int, default=0, help="override samples per layer")
     ap.add_argument("--layers", type=int, default=0, help="first n layers only (small profiling cases)")
+    ap.add_argument("--hist", default="auto", choices=["auto", "smem", "global"],
+                    help="count histogram: library choice, shared-memory privatised, or L2 reductions")
     ap.add_argument("--spt", type=int, default=0, help="samples per thread (0 = library choice)")
     ap.add_argument("--router-samples", type=int, default=10**7, help="labelled pairs for the router form")
     return ap.parse_args()
@@ -432,7 +434,8 @@ def main():
         ri = router.info()
         router_info = {"train_samples": args.router_samples, "train_accuracy": ri.train_accuracy,
                        "train_loss": ri.train_loss, "build_ms": ri.build_ms, "neighbours": ri.neighbours}
-    opts = B.options(form=form, prec=prec, samples_per_thread=args.spt, counts_type=ctype,
+    hist_flags = {"auto": 0, "smem": B.FLAG_SMEM_HIST, "global": B.FLAG_GLOBAL_HIST}[args.hist]
+    opts = B.options(form=form, prec=prec, samples_per_thread=args.spt, counts_type=ctype, flags=hist_flags,
                      router=router.handle if router else None)
     counts = torch.empty(entries, dtype=torch.int64 if ctype == B.COUNTS_I64 else torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # larger than the 129 MB L2
