@@ -752,6 +752,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
             c.recs = p.rec32 + (gr == 0 ? S.roffA : S.roffB) * F;
             c.chunk_ok = c0 >= 0 && c0 < c.nch;
             c.mbc = c.chunk_ok ? c0 : 0;
+        };
+        // the FP32 re-score of the best chunk (records from L2) and the certificate
+        auto score = [&](Pass& c) {
             cc_chunk<DM>(c.recs, c.mbc, c.x, c.idx, c.best, c.in2, c.r1);
             // FP32 inside the best chunk, tensor-core scores outside it
             c.why = 0;
@@ -882,9 +885,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
             first(s, 0, S, pa);
             first(s, 1, S, pb);
             // the chunk states and the item slot are read (the passes hold copies):
-            // release them at once, so that the epilogue and the next item can move in
+            // release them before the L2 loads of the re-score, so that the epilogue
+            // and the next item can move in
             mbar_arrive(smem_u32(&s_stempty[s]));
             if constexpr (!DRAW_IN) mbar_arrive(smem_u32(&s_certdone[s]));   // the draw pass may refill the slot
+            score(pa);
+            score(pb);
             int ci = finish(pa, S.NA, valid, needA);
             int cj = finish(pb, S.NB, valid, needB);
             recheck(pa, 0, S, ms, needA, ci);
