@@ -369,6 +369,9 @@ def extra_workloads(ctx, B, dev, stream, flush, peaks, n_sm):
     out["ou2_alg3"], g2 = run("ou2", m2, 5, 3, B.options(form=B.FORM_F32_RECHECK, prec=m2.prec))
     out["ou2_alg2_pathwise"], _ = run("ou2", m2, 5, 3, B.options(prec=m2.prec), pathwise=True)
     out["ou2_alg2_pathwise"]["vs_alg3"] = out["ou2_alg2_pathwise"]["value"] / out["ou2_alg3"]["value"]
+    # Algorithm II on the 8-d chain (grids streamed through shared memory), M = 10^7
+    m8 = W.ar8(M=10**7)
+    out["ar8_alg2_pathwise_M1e7"], _ = run("ar8", m8, 2, 1, B.options(prec=m8.prec), pathwise=True)
     # the paper's scenario (d = 2, n = 365, M = 10^5, N = 500): Algorithm III and II
     mp = W.paper(N=500)
     out["paper_alg3"], _ = run("paper", mp, 5, 3, B.options(prec=mp.prec))

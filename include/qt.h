@@ -216,8 +216,8 @@ QT_API qt_status qt_transitions(qt_ctx* ctx, const qt_model* model, const double
  *          acc += t_lq*eps_q (q <= l).
  *   opts   form QT_FORM_AUTO or QT_FORM_F32_RECHECK (FP32 screen with the exact
  *          recheck: cells exact under the library contract); FP32 or FP64
- *          samples.  Each grid's FP32 records must fit half of one CTA's
- *          shared memory, else QT_EUNSUPPORTED.
+ *          samples.  Grids of any size (streamed through shared memory in
+ *          segments when they exceed half of it).
  *   counts, dump, stats as in qt_transitions (dump row k holds X_k, X_{k+1}
  *          and their cells); model->m and L are read for layer 0 only.      */
 typedef struct {

@@ -443,17 +443,21 @@ qt_status make_plan_full(qt_ctx* ctx, int d, int n, const int64_t* Ns, const dou
         const bool f32 = o->sample_prec == QT_PREC_F32;
         P.form = kPathwise;
         const size_t rec_bytes = (size_t)P.rec_floats * 4;
-        size_t gmax = 0;
-        for (int g = 0; g <= n; ++g) gmax = std::max(gmax, (size_t)P.grids[g].Npad * rec_bytes);
+        long long npmax = 0;
+        for (int g = 0; g <= n; ++g) npmax = std::max<long long>(npmax, P.grids[g].Npad);
         const size_t budget = ctx->smem_optin > 24 * 1024 ? ctx->smem_optin - 24 * 1024 : 0;
-        P.grid_bytes = 2 * round_up((long long)gmax, 128);
-        if (P.grid_bytes > budget)
-            return fail(ctx, QT_EUNSUPPORTED,
-                        "the path-wise form keeps two grids in shared memory: %zu bytes exceed %zu", P.grid_bytes,
-                        budget);
+        // segments of whole grids when the largest fits half the shared memory,
+        // else the largest multiple of a chunk that does
+        long long seg = npmax;
+        if (2 * round_up(seg * (long long)rec_bytes, 128) > (long long)budget)
+            seg = (long long)(budget / 2 / rec_bytes) / kChunk * kChunk;
+        if (seg < kChunk) return fail(ctx, QT_EUNSUPPORTED, "records too large for the path-wise segments");
+        P.seg_records = (int)seg;
+        P.streamed = seg < npmax;
+        P.grid_bytes = 2 * round_up(seg * (long long)rec_bytes, 128);
         int S = o->tile_samples_per_thread > 0 ? o->tile_samples_per_thread
-                                                : pathwise_default_spt(P.dm, f32, M, 2ll * ctx->num_sms);
-        if (!pathwise_variant_exists(P.dm, S, f32))
+                                                : pathwise_default_spt(P.dm, f32, P.streamed, M, 2ll * ctx->num_sms);
+        if (!pathwise_variant_exists(P.dm, S, f32, P.streamed))
             return fail(ctx, QT_EUNSUPPORTED, "no path-wise kernel for d %d, %d paths per thread", d, S);
         P.S = S;
         P.block = 256;

@@ -45,7 +45,8 @@ cudaError_t forward_launch(int form, int dm, int S, bool streamed, const Forward
 {
     if (form == kTcRecheck) return launch_tc_forward(dm, p, dyn_smem, num_sms, blocks_per_sm, st);
     if (form == kRouterCert) return launch_router_forward(dm, p, num_sms, blocks_per_sm, st);
-    if (form == kPathwise) return launch_pathwise(dm, S, p.prec == 1, p, dyn_smem, num_sms, blocks_per_sm, st);
+    if (form == kPathwise)
+        return launch_pathwise(dm, S, p.prec == 1, streamed, p, dyn_smem, num_sms, blocks_per_sm, st);
     if (streamed) {
         if (form != kF32Recheck) return cudaErrorInvalidValue;
         return launch_f32_streamed(dm, S, p, block, dyn_smem, num_sms, blocks_per_sm, st);

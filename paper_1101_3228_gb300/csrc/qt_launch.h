@@ -26,10 +26,10 @@ cudaError_t launch_tc_forward_drawin(int dm, const ForwardParams& p, int dyn, in
 // draw pass of the tensor-core form over the items [p.item_lo, p.item_hi)
 cudaError_t launch_tc_draw(int dm, const ForwardParams& p, cudaStream_t st);
 // Algorithm II (path-wise): compiled variants, default paths per thread, launch
-bool pathwise_variant_exists(int dm, int S, bool f32);
-int pathwise_default_spt(int dm, bool f32, long long M, long long ctas);
-cudaError_t launch_pathwise(int dm, int S, bool f32, const ForwardParams& p, int dyn, int num_sms, int* bps,
-                            cudaStream_t st);
+bool pathwise_variant_exists(int dm, int S, bool f32, bool streamed);
+int pathwise_default_spt(int dm, bool f32, bool streamed, long long M, long long ctas);
+cudaError_t launch_pathwise(int dm, int S, bool f32, bool streamed, const ForwardParams& p, int dyn, int num_sms,
+                            int* bps, cudaStream_t st);
 cudaError_t launch_f32_streamed(int dm, int S, const ForwardParams& p, int block, int dyn, int num_sms, int* bps,
                                 cudaStream_t st);
 

@@ -19,12 +19,13 @@
 //
 // GB300 layout: one persistent kernel; a work item is a tile of paths
 // (256 threads x S paths), handed out by an L2 atomic counter.  A CTA carries
-// its tile through all layers: the FP32 records of Gamma_{g} sit in shared
-// memory buffer g & 1, and the bulk copy (TMA engine) of Gamma_{g+1} into the
-// other buffer overlaps the search in Gamma_g.  The search is the FP32 screen
-// with its certificate and the exact window search of the Algorithm III kernel
-// (qt_forward.cuh), so every cell is the exact FP64 cell of the library
-// contract.  Counts go to L2 with red.global.add (every CTA touches every
+// its tile through all layers.  The FP32 records of the grids go through two
+// shared-memory buffers as a sequence of segments (a whole grid per segment
+// when it fits half the shared memory, else several): while the CTA screens one
+// segment, the bulk copy (TMA engine) of the next is in flight.  The search is
+// the FP32 screen with its certificate and the exact window search of the
+// Algorithm III kernel (qt_forward.cuh), so every cell is the exact FP64 cell
+// of the library contract.  Counts go to L2 with red.global.add (every CTA touches every
 // layer, so a private histogram would be flushed n times per tile).
 #include "qt_forward.cuh"
 #include "qt_launch.h"
@@ -217,20 +218,21 @@ struct SampleType<true> {
 
 }  // namespace
 
-template <int DM, int S, bool F32>
+template <int DM, int S, bool F32, bool STREAMED>
 __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const ForwardParams p)
 {
     using T = typename SampleType<F32>::T;
+    constexpr int F = Rec32<DM>::kFloats;
     extern __shared__ __align__(128) unsigned char dsm_pw[];
     __shared__ __align__(8) unsigned long long s_bar[2];
     __shared__ long long s_item;
     __shared__ int s_abort;
-    __shared__ GridInfo s_G[2];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int d = p.d;
     const int n = p.n;
+    const int seg = p.seg_records;                       // records per segment, a multiple of kChunk
     const uint32_t buf_bytes = (uint32_t)p.smem_grid_bytes / 2u;
     const bool euler = p.pathwise_euler != 0;
 
@@ -241,29 +243,29 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const 
         s_abort = 0;
     }
     __syncthreads();
+    // the segment sequence of an item: grids 0..n in order, each in ceil(Npad / seg)
+    // segments; segment number c of the sequence goes to buffer c & 1
+    auto nseg = [&](int g) { return (p.grids[g].Npad + seg - 1) / seg; };
+    long long total_segs = 0;
+    for (int g = 0; g <= n; ++g) total_segs += nseg(g);
     uint32_t phase[2] = {0u, 0u};
     bool pending[2] = {false, false};
+    int sg = 0, st_seg = 0;                              // staging cursor (thread 0)
 
-    // bulk copy of grid g's FP32 records into buffer g & 1 (one thread)
-    auto stage = [&](int g) {
-        const GridInfo& G = p.grids[g];
-        const uint32_t bytes = (uint32_t)G.Npad * Rec32<DM>::kFloats * 4u;
-        const uint32_t bar = smem_u32(&s_bar[g & 1]);
+    // bulk copy of the next segment of the sequence into buffer c & 1 (thread 0)
+    auto stage_next = [&](long long c) {
+        const GridInfo& G = p.grids[sg];
+        const int first = st_seg * seg;
+        const int cnt = min(seg, G.Npad - first);
+        const uint32_t bytes = (uint32_t)cnt * F * 4u;
+        const uint32_t bar = smem_u32(&s_bar[c & 1]);
         fence_proxy_async();
         mbar_arrive_expect_tx(bar, bytes);
-        bulk_g2s(smem_u32(dsm_pw + (g & 1) * buf_bytes), p.rec32 + G.roff * Rec32<DM>::kFloats, bytes, bar);
-    };
-    // wait for grid g (every thread); a thread that gives up raises the CTA's
-    // abort flag, which every thread reads after the next barrier
-    auto await = [&](int g) {
-        const int b = g & 1;
-        if (!mbar_wait_bounded(smem_u32(&s_bar[b]), phase[b], p.spin_budget)) {
-            record_error(p.status, 4 /* QT_ETIMEOUT */, 40);
-            s_abort = 1;
-            mbar_wait_bounded(smem_u32(&s_bar[b]), phase[b], kDrainUs);
+        bulk_g2s(smem_u32(dsm_pw + (c & 1) * buf_bytes), p.rec32 + (G.roff + first) * F, bytes, bar);
+        if (++st_seg == nseg(sg)) {
+            st_seg = 0;
+            ++sg;
         }
-        phase[b] ^= 1u;
-        pending[b] = false;
     };
 
     while (true) {
@@ -272,15 +274,17 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const 
             if (*((volatile int32_t*)&p.status->code) == 0) it = (long long)atomicAdd(&p.status->queue, 1ull);
             s_item = it;
             if (it >= 0 && it < p.total_items) {
-                stage(0);
-                if (n >= 1) stage(1);
+                sg = 0;
+                st_seg = 0;
+                stage_next(0);
+                if (total_segs > 1) stage_next(1);
             }
         }
         __syncthreads();
         const long long item = s_item;
         if (item < 0 || item >= p.total_items) break;
         pending[0] = true;
-        pending[1] = n >= 1;
+        pending[1] = total_segs > 1;
 
         const unsigned long long mtile = (unsigned long long)item * (unsigned long long)p.tile;
         unsigned long long ms[S];
@@ -300,12 +304,13 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const 
             else path_start_f64<DM>(p.params_d, d, p.seed, m, x[s]);
         }
         bool aborted = false;
+        long long cur = 0;                               // next segment of the sequence to scan
         // ---- g = 0: the cell of X_0; g = k + 1: step k, then the cell of X_{k+1}
-        for (int g = 0; g <= n; ++g) {
+        for (int g = 0; g <= n && !aborted; ++g) {
             const int k = g - 1;
-            const float* gpf = p.params_f + (long long)(k < 0 ? 0 : k) * p.params_stride;
-            const double* gpd = p.params_d + (long long)(k < 0 ? 0 : k) * p.params_stride;
             if (k >= 0) {
+                const float* gpf = p.params_f + (long long)k * p.params_stride;
+                const double* gpd = p.params_d + (long long)k * p.params_stride;
                 // dump row k: X_k before the step
                 if (p.dump_count > 0) {
 #pragma unroll
@@ -324,23 +329,8 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const 
                     else path_step_f64<DM>(gpd, d, euler, p.seed, k, m, x[s]);
                 }
             }
-            if (tid == 0) {
-                s_G[g & 1] = p.grids[g];
-            }
-            await(g);
-            __syncthreads();
-            if (s_abort) {
-                aborted = true;
-                break;
-            }
-            // prefetch grid g + 1 into the other buffer (free: its last reader,
-            // the search in grid g - 1, finished before the barrier above)
-            if (g >= 1 && g + 1 <= n) {
-                if (tid == 0) stage(g + 1);
-                pending[(g + 1) & 1] = true;
-            }
-            const GridInfo& G = s_G[g & 1];
-            // ---- centre on Gamma_g and screen
+            const GridInfo& G = p.grids[g];
+            // ---- centre on Gamma_g
             float xa[S][DM], Aa[S];
 #pragma unroll
             for (int s = 0; s < S; ++s) {
@@ -357,23 +347,87 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const 
                 }
                 Aa[s] = __fsqrt_rn(na);
             }
-            const float* rec = reinterpret_cast<const float*>(dsm_pw + (g & 1) * buf_bytes);
+            // ---- FP32 screen over the grid's segments; the best chunk is resolved
+            // while its segment is in shared memory (a grid in one segment: after
+            // the scan, with no resolution state live across it)
             ScanState<S> st;
+            ResolveState<S> rs;
             scan_init<S>(st);
-            screen_scan<DM, S>(rec, G.Npad / kChunk, 0, xa, st);
+            resolve_init<S>(rs);
+            const int Npad = G.Npad;
+            const int ns = nseg(g);
             int cj[S];
             bool need[S];
+            if (!STREAMED) {    // every grid is one segment
+                const int b = (int)(cur & 1);
+                if (!mbar_wait_bounded(smem_u32(&s_bar[b]), phase[b], p.spin_budget)) {
+                    record_error(p.status, 4 /* QT_ETIMEOUT */, 40);
+                    s_abort = 1;
+                    mbar_wait_bounded(smem_u32(&s_bar[b]), phase[b], kDrainUs);
+                }
+                phase[b] ^= 1u;
+                pending[b] = false;
+                __syncthreads();
+                if (s_abort) break;
+                const float* rec = reinterpret_cast<const float*>(dsm_pw + b * buf_bytes);
+                screen_scan<DM, S>(rec, Npad / kChunk, 0, xa, st);
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                int idx;
-                float S1, r1;
-                resolve_one<DM>(rec, st.bc[s], xa[s], st.B1[s], idx, S1, r1);
-                const float second = fminf(st.B2[s], S1);
-                const bool cert = idx >= 0 && screen_certified(d, Aa[s], st.B1[s], second, r1);
-                cj[s] = idx;
-                need[s] = !cert && valid[s];
+                for (int s = 0; s < S; ++s) {
+                    int idx;
+                    float S1, r1;
+                    resolve_one<DM>(rec, st.bc[s], xa[s], st.B1[s], idx, S1, r1);
+                    const float second = fminf(st.B2[s], S1);
+                    const bool cert = idx >= 0 && screen_certified(d, Aa[s], st.B1[s], second, r1);
+                    cj[s] = idx;
+                    need[s] = !cert && valid[s];
+                }
+                __syncthreads();   // every warp is done with buffer b
+                if (cur + 2 < total_segs) {
+                    if (tid == 0) stage_next(cur + 2);
+                    pending[b] = true;
+                }
+                ++cur;
             }
-            // ---- exact window search of the uncertified, one warp per search
+            for (int t = 0; STREAMED && t < ns; ++t) {
+                const int b = (int)(cur & 1);
+                if (!mbar_wait_bounded(smem_u32(&s_bar[b]), phase[b], p.spin_budget)) {
+                    // give up: raise the CTA's abort flag (read by every thread after
+                    // the barrier) and let the copy land
+                    record_error(p.status, 4 /* QT_ETIMEOUT */, 40);
+                    s_abort = 1;
+                    mbar_wait_bounded(smem_u32(&s_bar[b]), phase[b], kDrainUs);
+                }
+                phase[b] ^= 1u;
+                pending[b] = false;
+                __syncthreads();
+                if (s_abort) {
+                    aborted = true;
+                    break;
+                }
+                const float* rec = reinterpret_cast<const float*>(dsm_pw + b * buf_bytes);
+                const int cnt = min(seg, Npad - t * seg);
+                const int c0 = t * seg / kChunk;
+                screen_scan<DM, S>(rec, cnt / kChunk, c0, xa, st);
+                screen_resolve<DM, S>(rec, cnt / kChunk, c0, xa, st, rs);
+                __syncthreads();   // every warp is done with buffer b
+                if (cur + 2 < total_segs) {
+                    if (tid == 0) stage_next(cur + 2);
+                    pending[b] = true;
+                }
+                ++cur;
+            }
+            if (aborted) break;
+            if (STREAMED) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    const float second = fminf(st.B2[s], rs.S1[s]);
+                    const bool cert = rs.idx[s] >= 0 && screen_certified(d, Aa[s], st.B1[s], second, rs.r1[s]);
+                    cj[s] = rs.idx[s];
+                    need[s] = !cert && valid[s];
+                }
+            }
+            // ---- exact window search of the uncertified, one warp per search (records from L2)
+            const float* grec = p.rec32 + G.roff * F;
 #pragma unroll
             for (int s = 0; s < S; ++s) {
                 unsigned mask = __ballot_sync(0xFFFFFFFFu, need[s]);
@@ -384,8 +438,7 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const 
                 while (mask) {
                     const int src = __ffs(mask) - 1;
                     mask &= mask - 1;
-                    const int r = warp_window_nn<DM>(xa[s], Aa[s], z, src, rec, G.Npad, p.g64 + G.goff * d,
-                                                     G.N, d);
+                    const int r = warp_window_nn<DM>(xa[s], Aa[s], z, src, grec, Npad, p.g64 + G.goff * d, G.N, d);
                     if (lane == src) cj[s] = r;
                     if (lane == 0) atomicAdd(&p.status->rechecks, 1ull);
                 }
@@ -394,7 +447,7 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const 
 #pragma unroll
             for (int s = 0; s < S; ++s) {
                 if (!valid[s]) {
-                    cell[s] = cj[s];
+                    cell[s] = 0;
                     continue;
                 }
                 const int j = cj[s];
@@ -411,8 +464,7 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const 
                         const unsigned long long t = ms[s] / (unsigned long long)p.dump_stride;
                         if (t < (unsigned long long)p.dump_count) {
                             const long long row = (long long)k * p.dump_count + (long long)t;
-                            for (int l = 0; l < d; ++l)
-                                p.dumpY[row * d + l] = (double)x[s][l];
+                            for (int l = 0; l < d; ++l) p.dumpY[row * d + l] = (double)x[s][l];
                             p.dumpI[row] = i;
                             p.dumpJ[row] = j;
                         }
@@ -420,7 +472,6 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const 
                 }
                 cell[s] = j;
             }
-            __syncthreads();   // every warp is done with buffer g & 1
         }
         if (aborted) {
             // let the copies still in flight land before the CTA leaves
@@ -431,10 +482,10 @@ __global__ void __launch_bounds__(256, (DM <= 4 ? 2 : 1)) pathwise_kernel(const 
     }
 }
 
-template <int DM, int S, bool F32>
+template <int DM, int S, bool F32, bool STREAMED>
 static cudaError_t launch_pw(const ForwardParams& p, int dyn, int num_sms, int* bps, cudaStream_t st)
 {
-    auto kern = pathwise_kernel<DM, S, F32>;
+    auto kern = pathwise_kernel<DM, S, F32, STREAMED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
     int b = 0;
@@ -449,49 +500,69 @@ static cudaError_t launch_pw(const ForwardParams& p, int dyn, int num_sms, int* 
     return cudaGetLastError();
 }
 
-// Compiled (dimension class, paths per thread) pairs: FP32 samples for every
-// class, FP64 samples for the small classes (the 1-d FP64 workload and tests).
+// Compiled (dimension class, paths per thread) pairs: grids resident in one
+// segment each (FP32 samples for every class, FP64 samples for the small
+// classes), and grids streamed in several segments (one choice per class).
 static const int kPwF32[][2] = {{1, 8}, {1, 2}, {2, 8}, {2, 4}, {2, 2}, {2, 1}, {3, 4}, {4, 4}, {4, 1},
                                 {6, 2}, {8, 2}, {8, 1}, {10, 2}, {10, 1}, {12, 1}, {16, 1}};
 static const int kPwF64[][2] = {{1, 4}, {1, 1}, {2, 4}, {2, 1}, {4, 2}, {8, 1}};
+static const int kPwStreamF32[][2] = {{1, 4}, {2, 4}, {3, 4}, {4, 4}, {6, 2}, {8, 2}, {10, 2}, {12, 1}, {16, 1}};
+static const int kPwStreamF64[][2] = {{1, 2}, {2, 2}, {4, 1}, {8, 1}};
 
-bool pathwise_variant_exists(int dm, int S, bool f32)
+bool pathwise_variant_exists(int dm, int S, bool f32, bool streamed)
 {
-    if (f32) {
-        for (const auto& t : kPwF32)
-            if (t[0] == dm && t[1] == S) return true;
-    } else {
-        for (const auto& t : kPwF64)
-            if (t[0] == dm && t[1] == S) return true;
-    }
-    return false;
+    auto in = [&](const int (*tab)[2], int count) {
+        for (int i = 0; i < count; ++i)
+            if (tab[i][0] == dm && tab[i][1] == S) return true;
+        return false;
+    };
+    if (streamed)
+        return f32 ? in(kPwStreamF32, (int)(sizeof kPwStreamF32 / sizeof kPwStreamF32[0]))
+                   : in(kPwStreamF64, (int)(sizeof kPwStreamF64 / sizeof kPwStreamF64[0]));
+    return f32 ? in(kPwF32, (int)(sizeof kPwF32 / sizeof kPwF32[0]))
+               : in(kPwF64, (int)(sizeof kPwF64 / sizeof kPwF64[0]));
 }
 
-// Paths per thread: the register-budget choice, lowered while the path tiles
-// would not give every CTA slot (ctas = SMs x resident CTAs) about two tiles --
-// the path-wise form has only M paths of parallelism.
-int pathwise_default_spt(int dm, bool f32, long long M, long long ctas)
+// Paths per thread: the register-budget choice (the compiled one when the grids
+// are streamed), lowered while the path tiles would not give every CTA slot
+// (ctas = SMs x resident CTAs) about two tiles -- the path-wise form has only
+// M paths of parallelism.
+int pathwise_default_spt(int dm, bool f32, bool streamed, long long M, long long ctas)
 {
-    int S = f32 ? (dm <= 2 ? 8 : (dm <= 4 ? 4 : (dm <= 10 ? 2 : 1))) : (dm <= 2 ? 4 : (dm <= 4 ? 2 : 1));
+    int S;
+    if (streamed) {
+        S = 1;
+        for (int c : {4, 2, 1})
+            if (pathwise_variant_exists(dm, c, f32, true)) {
+                S = c;
+                break;
+            }
+        return S;
+    }
+    S = f32 ? (dm <= 2 ? 8 : (dm <= 4 ? 4 : (dm <= 10 ? 2 : 1))) : (dm <= 2 ? 4 : (dm <= 4 ? 2 : 1));
     while (S > 1) {
         const int next = S / 2;
-        if (M >= 2ll * ctas * 256 * S || !pathwise_variant_exists(dm, next, f32)) break;
+        if (M >= 2ll * ctas * 256 * S || !pathwise_variant_exists(dm, next, f32, false)) break;
         S = next;
     }
     return S;
 }
 
-cudaError_t launch_pathwise(int dm, int S, bool f32, const ForwardParams& p, int dyn, int num_sms, int* bps,
-                            cudaStream_t st)
+cudaError_t launch_pathwise(int dm, int S, bool f32, bool streamed, const ForwardParams& p, int dyn, int num_sms,
+                            int* bps, cudaStream_t st)
 {
-#define QT_CASE(D, SS, F) \
-    if (dm == D && S == SS && f32 == F) return launch_pw<D, SS, F>(p, dyn, num_sms, bps, st);
-    QT_CASE(1, 8, true) QT_CASE(1, 2, true) QT_CASE(2, 8, true) QT_CASE(2, 4, true) QT_CASE(2, 2, true)
-    QT_CASE(2, 1, true) QT_CASE(3, 4, true) QT_CASE(4, 4, true) QT_CASE(4, 1, true) QT_CASE(6, 2, true)
-    QT_CASE(8, 2, true) QT_CASE(8, 1, true) QT_CASE(10, 2, true) QT_CASE(10, 1, true) QT_CASE(12, 1, true)
-    QT_CASE(16, 1, true)
-    QT_CASE(1, 4, false) QT_CASE(1, 1, false) QT_CASE(2, 4, false) QT_CASE(2, 1, false) QT_CASE(4, 2, false)
-    QT_CASE(8, 1, false)
+#define QT_CASE(D, SS, F, ST) \
+    if (dm == D && S == SS && f32 == F && streamed == ST) return launch_pw<D, SS, F, ST>(p, dyn, num_sms, bps, st);
+    QT_CASE(1, 8, true, false) QT_CASE(1, 2, true, false) QT_CASE(2, 8, true, false) QT_CASE(2, 4, true, false)
+    QT_CASE(2, 2, true, false) QT_CASE(2, 1, true, false) QT_CASE(3, 4, true, false) QT_CASE(4, 4, true, false)
+    QT_CASE(4, 1, true, false) QT_CASE(6, 2, true, false) QT_CASE(8, 2, true, false) QT_CASE(8, 1, true, false)
+    QT_CASE(10, 2, true, false) QT_CASE(10, 1, true, false) QT_CASE(12, 1, true, false) QT_CASE(16, 1, true, false)
+    QT_CASE(1, 4, false, false) QT_CASE(1, 1, false, false) QT_CASE(2, 4, false, false) QT_CASE(2, 1, false, false)
+    QT_CASE(4, 2, false, false) QT_CASE(8, 1, false, false)
+    QT_CASE(1, 4, true, true) QT_CASE(2, 4, true, true) QT_CASE(3, 4, true, true) QT_CASE(4, 4, true, true)
+    QT_CASE(6, 2, true, true) QT_CASE(8, 2, true, true) QT_CASE(10, 2, true, true) QT_CASE(12, 1, true, true)
+    QT_CASE(16, 1, true, true)
+    QT_CASE(1, 2, false, true) QT_CASE(2, 2, false, true) QT_CASE(4, 1, false, true) QT_CASE(8, 1, false, true)
 #undef QT_CASE
     return cudaErrorInvalidValue;
 }

@@ -2,8 +2,9 @@
 Wilbertz, arXiv:1101.3228) through the C ABI against the CPU oracle: counts bit
 for bit, path states and cells of dumped paths bit for bit, for the AR(1)
 chain of Prop. 1 and for the Euler-scheme (square-root) chain that is not
-AR(1); FP32 and FP64 samples; the full 2-factor workload in the benchmark's
-launch configuration; the unsupported requests and the timeout path.
+AR(1); FP32 and FP64 samples; grids streamed in segments; the full 2-factor
+workload in the benchmark's launch configuration; the unsupported requests and
+the timeout path.
 """
 import numpy as np
 import pytest
@@ -134,11 +135,21 @@ def test_pathwise_unsupported_requests(ctx, B):
     with pytest.raises(B.QtError) as e:
         ctx.transitions_pathwise(model, g, model.M, model.seed, B.options(form=B.FORM_TC_RECHECK))
     assert e.value.status == B.QT_EUNSUPPORTED
-    big = W.ar8(M=100).restrict(n=2, N=4000)      # 4000 x 48 bytes x 2 buffers > shared memory
-    gb = _dev(W.layer_grids(big, samples=12000, iters=1))
-    with pytest.raises(B.QtError) as e:
-        ctx.transitions_pathwise(big, gb, big.M, big.seed)
-    assert e.value.status == B.QT_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("name,n,N,M", [("ar8", 3, 4000, 4001), ("maxcall10", 2, 8000, 2001),
+                                         ("basket4", 50, 0, 1501)])
+def test_pathwise_streamed_grids_bit_exact(ctx, B, name, n, N, M):
+    """Grids larger than half of the shared memory (8-d N = 4000, 10-d N = 8000) go
+    through the two buffers in segments (layer 0's one-point grid in one); the 4-d
+    basket's uneven grids (N_k up to 2000) fit whole.  Counts against the oracle."""
+    full = W.get(name, M=M)
+    model = full.restrict(n=n, N=N) if N else full.restrict(n=n)
+    g = W.layer_grids(model, samples=3 * int(np.max(model.N)), iters=2)
+    counts, stats, _ = ctx.transitions_pathwise(model, _dev(g), model.M, model.seed)
+    assert stats.device_status == 0
+    ref = oracle.pathwise(model, g, model.M, model.seed, oracle.PREC_F32)
+    _check_counts(B, model, counts, ref)
 
 
 def test_pathwise_timeout_is_reported_and_context_survives(ctx, B):
