@@ -24,9 +24,9 @@
 //                    copies them into the item slots with bulk copies.
 // The roles of the screen kernel meet only at mbarriers:
 //     two MMA warps        one per epilogue warpgroup; tile g of the CTA's
-//                          sequence goes to warpgroup g & 1, its two 128-point
-//                          halves to that warpgroup's two 128-column TMEM
-//                          accumulators (four in all);
+//                          sequence goes to warpgroup g & 1, its 256 points in
+//                          kAccN-point slices to that warpgroup's kAccPerWg
+//                          TMEM accumulators (512 columns in all);
 //     a loader warp        bulk copies of the grids' operand tiles, kept for
 //                          the whole layer when both grids fit, else streamed
 //                          through a ring;
@@ -261,7 +261,10 @@ constexpr int kMmaWarp0 = 8;       // warps 8, 9: MMAs for epilogue warpgroups 0
 constexpr int kLoadWarp = 10;      // warp 10: bulk copies of the operand tiles
 constexpr int kOpWarp = 11;        // warp 11: bulk copies of each item's drawn samples (draw pass layout)
 constexpr int kCertWarp0 = 12;     // warps 12-15: (draw,) certify, recheck, count
-constexpr int kHalfN = kTcTileN / 2;   // columns of one accumulator (MMA N)
+constexpr int kAccN = 256;             // columns of one accumulator (MMA N): a whole tile
+constexpr int kAccPerWg = kTcTileN / kAccN;   // accumulators per epilogue warpgroup (one tile)
+constexpr int kAccs = 2 * kAccPerWg;   // 512 TMEM columns in all
+static_assert(kAccs * kAccN == 2 * kTcTileN && kAccN % 64 == 0, "accumulator layout");
 static_assert(kTcThreads == 16 * 32, "role layout");
 
 // What a certifier warp needs of the layer of an item (shared memory, one per
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
     const float kInf = __int_as_float(0x7F800000);
     extern __shared__ __align__(128) unsigned char dsm_tc[];
     __shared__ __align__(8) unsigned long long s_tfull[kTcMaxSlots], s_tempty[kTcMaxSlots];
-    __shared__ __align__(8) unsigned long long s_accfull[4], s_accempty[4];
+    __shared__ __align__(8) unsigned long long s_accfull[kAccs], s_accempty[kAccs];
     __shared__ __align__(8) unsigned long long s_opfull[2], s_opempty[2];
     __shared__ __align__(8) unsigned long long s_stA[2], s_stB[2], s_stempty[2];
     __shared__ __align__(8) unsigned long long s_drain[2], s_ldone;
@@ -378,7 +381,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
             mbar_init(smem_u32(&s_tfull[i]), 1);
             mbar_init(smem_u32(&s_tempty[i]), 1);
         }
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < kAccs; ++a) {
             mbar_init(smem_u32(&s_accfull[a]), 1);
             mbar_init(smem_u32(&s_accempty[a]), 128);
         }
@@ -412,12 +415,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
     if (warp == kMmaWarp0 || warp == kMmaWarp0 + 1) {
         // ================================================================ MMAs
         // tile g of the CTA's sequence goes to warpgroup g & 1, which has its
-        // own issuing warp; the tile's two 128-point halves go to that
-        // warpgroup's accumulators 2 (g & 1) + h
+        // own issuing warp; slice h of the tile (kAccN points) goes to that
+        // warpgroup's accumulator kAccPerWg (g & 1) + h
         const int ib = warp - kMmaWarp0;
         if (lane == 0) {
             const bool resident = p.tc_resident != 0;
-            const uint32_t idesc = (1u << 4) | ((uint32_t)(kHalfN >> 3) << 17) | ((uint32_t)(kTcTileM >> 4) << 24);
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(kAccN >> 3) << 17) | ((uint32_t)(kTcTileM >> 4) << 24);
             int tA = 0, nT = 0, layers = 0, lastT = 0;
             long long lbeg = 0, lend = 0;
             uint32_t tph = 0, pend = 0;        // resident: parity of each slot's current load, slots not yet waited
@@ -480,8 +483,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                     }
                     const uint32_t a_base = ops_u + (uint32_t)((os * 2 + (i < tA ? 0 : 1)) * kOpBytes);
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int acc = 2 * ib + h;
+                    for (int h = 0; h < kAccPerWg; ++h) {
+                        const int acc = kAccPerWg * ib + h;
                         if (!mbar_wait_bounded(smem_u32(&s_accempty[acc]), (uint32_t)((gg >> 1) & 1) ^ 1u,
                                                p.spin_budget)) {
                             fail(23);
@@ -489,8 +492,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
                         }
                         tc_fence_after();
                         // rows 128h .. 128h + 127 of the tile: 16 row blocks of K * 16 bytes further
-                        const uint32_t b_base = ring_u + (uint32_t)(slot * kTileBytes + h * (kHalfN / 8) * K * 16);
-                        const uint32_t dt = tmem + (uint32_t)(acc * kHalfN);
+                        const uint32_t b_base = ring_u + (uint32_t)(slot * kTileBytes + h * (kAccN / 8) * K * 16);
+                        const uint32_t dt = tmem + (uint32_t)(acc * kAccN);
 #pragma unroll
                         for (int s = 0; s < KT; ++s) {
                             const uint64_t ad = smem_desc(a_base + s * 256, 128, K * 16);
@@ -607,22 +610,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) forward_tc_kernel(const Forward
         ChunkTrack tr;
         auto process = [&](long long gg, int lt) -> bool {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int acc = 2 * wg + h;
+            for (int h = 0; h < kAccPerWg; ++h) {
+                const int acc = kAccPerWg * wg + h;
                 if (!warp_wait(smem_u32(&s_accfull[acc]), (uint32_t)((gg >> 1) & 1), p.spin_budget)) return false;
                 tc_fence_after();
-                // all chunk minima of the half first, so that the accumulator goes
-                // back to the MMA warp before the tracking work
-                float mc[kHalfN / kChunk];
+                // all chunk minima of the accumulator first, so that it goes back to
+                // the MMA warp before the tracking work
+                float mc[kAccN / kChunk];
 #pragma unroll
-                for (int q = 0; q < kHalfN / 64; ++q)
-                    tc_chunk_min4(trow + (uint32_t)(acc * kHalfN + q * 64), mc[4 * q], mc[4 * q + 1], mc[4 * q + 2],
+                for (int q = 0; q < kAccN / 64; ++q)
+                    tc_chunk_min4(trow + (uint32_t)(acc * kAccN + q * 64), mc[4 * q], mc[4 * q + 1], mc[4 * q + 2],
                                   mc[4 * q + 3]);
                 tc_fence_before();
                 mbar_arrive(smem_u32(&s_accempty[acc]));
-                const int c0 = lt * (kTcTileN / kChunk) + h * (kHalfN / kChunk);
+                const int c0 = lt * (kTcTileN / kChunk) + h * (kAccN / kChunk);
 #pragma unroll
-                for (int q = 0; q < kHalfN / kChunk; ++q) tr.add(mc[q], c0 + q);
+                for (int q = 0; q < kAccN / kChunk; ++q) tr.add(mc[q], c0 + q);
             }
             return true;
         };
