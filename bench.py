@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--hist", default="auto", choices=["auto", "smem", "global"],
                     help="count histogram: library choice, shared-memory privatised, or L2 reductions")
     ap.add_argument("--spt", type=int, default=0, help="samples per thread (0 = library choice)")
+    ap.add_argument("--tc-draw", type=int, default=0, choices=[0, 1, 2],
+                    help="tensor-core form's sample-draw layout: 0 autotuned, 1 draw pass, 2 in the screen kernel")
     ap.add_argument("--router-samples", type=int, default=10**7, help="labelled pairs for the router form")
     return ap.parse_args()
 
@@ -88,18 +90,20 @@ def plain_form(model, B):
     return B.FORM_PLAIN_F64 if model.d <= 2 else B.FORM_F32_RECHECK
 
 
-def candidates_per_sample_layer(model):
-    """Brute-force candidate distances per sample.layer: N_k + N_{k+1}, averaged over layers."""
+def candidates_per_sample_layer(model, pathwise=False):
+    """Brute-force candidate distances per sample.layer, averaged over layers:
+    N_k + N_{k+1} for Algorithm III (both points of a pair are searched), N_{k+1}
+    for Algorithm II (one search per path and layer)."""
     N = np.asarray(model.N, dtype=np.float64)
-    return float(np.sum(N[:-1] + N[1:]) / model.n)
+    return float(np.sum(N[1:] if pathwise else N[:-1] + N[1:]) / model.n)
 
 
-def flops_per_sample_layer(model):
+def flops_per_sample_layer(model, pathwise=False):
     """Algorithmic work of the search: per candidate distance d subtractions (or
     the expanded form's d multiply-adds) and d multiply-adds, 2d flops (Sec. 4
     counts 6 operations for a 2-d distance including its comparison; the
     comparison is not counted here)."""
-    return candidates_per_sample_layer(model) * 2 * model.d
+    return candidates_per_sample_layer(model, pathwise) * 2 * model.d
 
 
 def tc_pipe_flops_per_sample_layer(model):
@@ -287,14 +291,16 @@ def tensor_roofline(model, units, kern_ms, peaks):
             if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)"}
 
 
-def alu_roofline(model, units, kern_ms, peaks, n_sm):
+def alu_roofline(model, units, kern_ms, peaks, n_sm, pathwise=False):
     """FP32 screen against the FP32 FMA lanes (SMs x 128 lanes x 2 flops x max clock)."""
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     peak = 2.0 * FP32_LANES_PER_SM * n_sm * sm_max * 1e6 / 1e12
-    ach = flops_per_sample_layer(model) * units / (kern_ms / 1e3) / 1e12
+    work = flops_per_sample_layer(model, pathwise)
+    ach = work * units / (kern_ms / 1e3) / 1e12
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "kernel_ms": kern_ms,
-            "work": f"{flops_per_sample_layer(model):.0f} flops per sample.layer (2d per candidate)",
+            "work": f"{work:.0f} flops per sample.layer (2d per candidate, "
+                    f"{candidates_per_sample_layer(model, pathwise):.0f} candidates)",
             "peak_basis": f"FP32 FMA lanes: {n_sm} SMs x {FP32_LANES_PER_SM} x 2 flops x {sm_max:.0f} MHz"}
 
 
@@ -353,7 +359,7 @@ def extra_workloads(ctx, B, dev, stream, flush, peaks, n_sm):
             r["tc_draw"] = {1: "draw pass", 2: "in the screen kernel"}.get(st.tc_draw)
             r["roofline"] = tensor_roofline(model, units, kmean, peaks)
         else:
-            r["roofline"] = alu_roofline(model, units, kmean, peaks, n_sm)
+            r["roofline"] = alu_roofline(model, units, kmean, peaks, n_sm, pathwise)
         del counts
         torch.cuda.empty_cache()
         return r, g
@@ -439,7 +445,7 @@ def main():
                        "train_loss": ri.train_loss, "build_ms": ri.build_ms, "neighbours": ri.neighbours}
     hist_flags = {"auto": 0, "smem": B.FLAG_SMEM_HIST, "global": B.FLAG_GLOBAL_HIST}[args.hist]
     opts = B.options(form=form, prec=prec, samples_per_thread=args.spt, counts_type=ctype, flags=hist_flags,
-                     router=router.handle if router else None)
+                     router=router.handle if router else None, tc_draw=args.tc_draw)
     counts = torch.empty(entries, dtype=torch.int64 if ctype == B.COUNTS_I64 else torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # larger than the 129 MB L2
     units = model.n * model.M
