@@ -336,8 +336,8 @@ def extra_workloads(ctx, B, dev, stream, flush, peaks, n_sm):
     import torch
     out = {}
 
-    def run(name, model, K, W_, o=None, pathwise=False):
-        g = bench_grids(ctx, B, model)
+    def run(name, model, K, W_, o=None, pathwise=False, grids=None):
+        g = grids if grids is not None else bench_grids(ctx, B, model)
         ct = counts_type_for(B, model, dev)
         o = o or B.options(prec=model.prec, counts_type=ct)
         o.counts_type = ct
@@ -355,6 +355,8 @@ def extra_workloads(ctx, B, dev, stream, flush, peaks, n_sm):
              "form": "pathwise_f32" if pathwise else B.FORM_NAMES.get(st.form_used, "?"),
              "counts": "int64" if ct == B.COUNTS_I64 else "uint32", "launches_per_step": st.launches,
              "rechecks_per_step": st.rechecks}
+        if st.form_used == B.FORM_ROUTER_CERT:
+            r["candidates_per_search"] = st.candidates / (2 * units)
         if st.form_used == B.FORM_TC_RECHECK and not pathwise:
             r["tc_draw"] = {1: "draw pass", 2: "in the screen kernel"}.get(st.tc_draw)
             r["roofline"] = tensor_roofline(model, units, kmean, peaks)
@@ -378,6 +380,22 @@ def extra_workloads(ctx, B, dev, stream, flush, peaks, n_sm):
     # Algorithm II on the 8-d chain (grids streamed through shared memory), M = 10^7
     m8 = W.ar8(M=10**7)
     out["ar8_alg2_pathwise_M1e7"], _ = run("ar8", m8, 2, 1, B.options(prec=m8.prec), pathwise=True)
+    # the learned router (MLP on the tensor cores) with the Elkan certificate on the
+    # 8-d chain at M = 10^7, trained on 10^7 labelled pairs, beside the FP32 screen
+    # on the same grids
+    m8r = W.ar8(M=10**7)
+    g8 = bench_grids(ctx, B, m8r)
+    t0 = time.perf_counter()
+    rt = ctx.router_train(m8r, g8, samples=10**7, layers=8, epochs=4, seed=7 + W.CONFIG_INDEX["ar8"])
+    ri = rt.info()
+    rr, _ = run("ar8", m8r, 2, 1, B.options(form=B.FORM_ROUTER_CERT, prec=m8r.prec, router=rt.handle), grids=g8)
+    rr["router"] = {"train_samples": 10**7, "train_accuracy": ri.train_accuracy, "train_loss": ri.train_loss,
+                    "build_s": time.perf_counter() - t0, "neighbours": ri.neighbours}
+    rf, _ = run("ar8", m8r, 2, 1, B.options(form=B.FORM_F32_RECHECK, prec=m8r.prec), grids=g8)
+    rr["f32_screen_value"] = rf["value"]
+    rr["vs_f32_screen"] = rr["value"] / rf["value"]
+    out["ar8_router_M1e7"] = rr
+    rt.close()
     # the paper's scenario (d = 2, n = 365, M = 10^5, N = 500): Algorithm III and II
     mp = W.paper(N=500)
     out["paper_alg3"], _ = run("paper", mp, 5, 3, B.options(prec=mp.prec))

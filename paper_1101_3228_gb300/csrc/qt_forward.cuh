@@ -522,16 +522,37 @@ __device__ __noinline__ int warp_window_nn(const float (&xs)[DM], float A, const
     }
     const float Av = __shfl_sync(0xFFFFFFFFu, A, src);
     const int lane = threadIdx.x & 31;
+    // a lane scores records j, j + 32, j + 64, j + 96 (loads in flight together),
+    // then takes them in increasing index order
+    constexpr int kU = 4;
+    auto score = [&](int j) {
+        const float4* r4 = reinterpret_cast<const float4*>(recs + (long long)j * F);
+        float f[F];
+#pragma unroll
+        for (int v = 0; v < F / 4; ++v) {
+            const float4 a = r4[v];
+            f[4 * v] = a.x;
+            f[4 * v + 1] = a.y;
+            f[4 * v + 2] = a.z;
+            f[4 * v + 3] = a.w;
+        }
+        float sc = f[0];
+#pragma unroll
+        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], f[1 + l], sc);
+        return sc;
+    };
     float b1 = __int_as_float(0x7F800000);
     int i1 = 0x7FFFFFFF;
-    for (int j = lane; j < N; j += 32) {
-        const float* r = recs + (long long)j * F;
-        float sc = r[0];
+    for (int j0 = lane; j0 < N; j0 += 32 * kU) {
+        float sc[kU];
 #pragma unroll
-        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], r[1 + l], sc);
-        if (sc < b1) {
-            b1 = sc;
-            i1 = j;
+        for (int u = 0; u < kU; ++u) sc[u] = score(min(j0 + 32 * u, N - 1));
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (j0 + 32 * u < N && sc[u] < b1) {
+                b1 = sc[u];
+                i1 = j0 + 32 * u;
+            }
         }
     }
 #pragma unroll
@@ -562,16 +583,19 @@ __device__ __noinline__ int warp_window_nn(const float (&xs)[DM], float A, const
     // exact distances on the window only
     double best = __longlong_as_double(0x7FF0000000000000LL);
     int bi = 0x7FFFFFFF;
-    for (int j = lane; j < N; j += 32) {
-        const float* rr = recs + (long long)j * F;
-        float sc = rr[0];
+    for (int j0 = lane; j0 < N; j0 += 32 * kU) {
+        float sc[kU];
 #pragma unroll
-        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], rr[1 + l], sc);
-        if (sc <= lim) {
-            const double dj = dist64<DM>(zz, g64 + (long long)j * d, d);
-            if (dj < best) {
-                best = dj;
-                bi = j;
+        for (int u = 0; u < kU; ++u) sc[u] = score(min(j0 + 32 * u, N - 1));
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int j = j0 + 32 * u;
+            if (j < N && sc[u] <= lim) {
+                const double dj = dist64<DM>(zz, g64 + (long long)j * d, d);
+                if (dj < best) {
+                    best = dj;
+                    bi = j;
+                }
             }
         }
     }

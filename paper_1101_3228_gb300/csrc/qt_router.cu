@@ -1,22 +1,18 @@
-// qt_router.cu -- learned start cell + Elkan certificate for the nearest-cell
-// search of Algorithm III (Pages & Wilbertz, arXiv:1101.3228, Sec. 3.2 uses
-// brute force; the paper's kd-tree attempt is the prior art for sub-linear
-// search).
+// qt_router.cu -- the learned router of the router form (a start cell for the
+// nearest-cell searches of Algorithm III, Pages & Wilbertz, arXiv:1101.3228,
+// Sec. 3.2; the paper's kd-tree attempt there is the prior art for a
+// sub-linear search): its tables and its training.  The search itself is in
+// qt_router_search.cu.
 //
 // Router: MLP d -> 64 -> 64 -> 64 (ReLU) on whitened coordinates
 // z = L_k^{-1}(x - mu_k); the output is one of 64 buckets, a k-means partition
 // of the grid points (the same index partition for every layer, since the
-// grids of the layers are images of one base grid).  Start cell i0 = nearest
-// member of the predicted bucket.
-// Certificate (triangle inequality): every j with |c_i0 - c_j| > r0 + r*
-// (r0 = |x - c_i0|, r* = best distance so far) is farther from x than the best
-// candidate, so walking the neighbours of i0 in increasing distance until that
-// bound finds the exact cell.  Distances are upper bounds from FP32 scores and
-// lower bounds of the neighbour distances, with a relative slack of 2^-20 that
-// keeps every excluded point farther also under the FP64 rounding of the exact
-// distance.  The candidates are screened in FP32 with the margin certificate of
-// the brute-force screen; an exhausted neighbour list or an uncertified margin
-// falls back to the exact FP64 search.
+// grids of the layers are images of one base grid).
+// Training: pairs drawn by the library's sampler, labelled with the bucket of
+// their exact cell (the library's own certified search), cross-entropy with
+// Adam, forward and backward passes in FP32 on the CUDA cores.
+// Elkan tables: per grid point its C nearest other points in increasing
+// distance (FP64 distances rounded down), the lists the certified walk scans.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -61,45 +57,7 @@ __global__ void grid_checksum_kernel(const double* __restrict__ g, long long cou
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
-// ------------------------------------------------------------------ MLP (shared by training and search)
-
-// Forward pass of one sample; W layout [out][in] row-major, packed.
-template <int DM>
-__device__ __forceinline__ void mlp_forward(const float* __restrict__ P, int d, const float (&z)[DM],
-                                            float (&h1)[kRtHidden], float (&h2)[kRtHidden],
-                                            float (&lg)[kRtBuckets])
-{
-    const float* W1 = P;
-    const float* b1 = W1 + kRtHidden * d;
-    const float* W2 = b1 + kRtHidden;
-    const float* b2 = W2 + kRtHidden * kRtHidden;
-    const float* W3 = b2 + kRtHidden;
-    const float* b3 = W3 + kRtHidden * kRtHidden;
-#pragma unroll
-    for (int o = 0; o < kRtHidden; ++o) {
-        float a = b1[o];
-#pragma unroll
-        for (int l = 0; l < DM; ++l)
-            if (l < d) a = fmaf(W1[o * d + l], z[l], a);
-        h1[o] = fmaxf(a, 0.0f);
-    }
-#pragma unroll
-    for (int o = 0; o < kRtHidden; ++o) h2[o] = b2[o];
-    for (int i = 0; i < kRtHidden; ++i) {
-        const float hi = h1[i];
-#pragma unroll
-        for (int o = 0; o < kRtHidden; ++o) h2[o] = fmaf(W2[o * kRtHidden + i], hi, h2[o]);
-    }
-#pragma unroll
-    for (int o = 0; o < kRtHidden; ++o) h2[o] = fmaxf(h2[o], 0.0f);
-#pragma unroll
-    for (int o = 0; o < kRtBuckets; ++o) lg[o] = b3[o];
-    for (int i = 0; i < kRtHidden; ++i) {
-        const float hi = h2[i];
-#pragma unroll
-        for (int o = 0; o < kRtBuckets; ++o) lg[o] = fmaf(W3[o * kRtHidden + i], hi, lg[o]);
-    }
-}
+// ------------------------------------------------------------------ MLP training (FP32, CUDA cores)
 
 // Training forward + loss: writes h1, h2 and dlogits = (softmax - onehot) / B.
 template <int DM>
@@ -313,398 +271,6 @@ __global__ void elkan_table_kernel(const double* __restrict__ grids, int d, int 
         nb_idx[base + c] = key == ~0ull ? i : (int32_t)(key & 0xFFFFFFFFu);
         nb_dist[base + c] = key == ~0ull ? __int_as_float(0x7F800000) : __uint_as_float((unsigned)(key >> 32));
     }
-}
-
-// ------------------------------------------------------------------ routed search kernel
-
-template <int DM>
-struct RouteOut {
-    int cell;       // certified cell, or -1 (exact fallback needed)
-    int cands;      // candidate distances evaluated
-};
-
-// Forward pass of the router on transposed weights (shared memory):
-// W1T[l][o], W2T[i][o], W3T[i][o], so that one hidden input feeds 64 outputs
-// through 16 float4 loads.  Returns the two largest logits' buckets.
-template <int DM>
-__device__ __forceinline__ void mlp_route(const float* __restrict__ T, int d, const float (&z)[DM], int& bk, int& bk2)
-{
-    const float* W1T = T;
-    const float* b1 = W1T + kRtHidden * d;
-    const float* W2T = b1 + kRtHidden;
-    const float* b2 = W2T + kRtHidden * kRtHidden;
-    const float* W3T = b2 + kRtHidden;
-    const float* b3 = W3T + kRtHidden * kRtHidden;
-    float h[kRtHidden], g[kRtHidden];
-#pragma unroll
-    for (int o = 0; o < kRtHidden; ++o) h[o] = b1[o];
-#pragma unroll
-    for (int l = 0; l < DM; ++l) {
-        if (l < d) {
-            const float4* w = reinterpret_cast<const float4*>(W1T + l * kRtHidden);
-#pragma unroll
-            for (int q = 0; q < kRtHidden / 4; ++q) {
-                const float4 v = w[q];
-                h[4 * q + 0] = fmaf(v.x, z[l], h[4 * q + 0]);
-                h[4 * q + 1] = fmaf(v.y, z[l], h[4 * q + 1]);
-                h[4 * q + 2] = fmaf(v.z, z[l], h[4 * q + 2]);
-                h[4 * q + 3] = fmaf(v.w, z[l], h[4 * q + 3]);
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 0; o < kRtHidden; ++o) {
-        h[o] = fmaxf(h[o], 0.0f);
-        g[o] = b2[o];
-    }
-#pragma unroll
-    for (int i = 0; i < kRtHidden; ++i) {
-        const float hi = h[i];
-        const float4* w = reinterpret_cast<const float4*>(W2T + i * kRtHidden);
-#pragma unroll
-        for (int q = 0; q < kRtHidden / 4; ++q) {
-            const float4 v = w[q];
-            g[4 * q + 0] = fmaf(v.x, hi, g[4 * q + 0]);
-            g[4 * q + 1] = fmaf(v.y, hi, g[4 * q + 1]);
-            g[4 * q + 2] = fmaf(v.z, hi, g[4 * q + 2]);
-            g[4 * q + 3] = fmaf(v.w, hi, g[4 * q + 3]);
-        }
-    }
-#pragma unroll
-    for (int o = 0; o < kRtHidden; ++o) {
-        g[o] = fmaxf(g[o], 0.0f);
-        h[o] = b3[o];                      // h now holds the logits
-    }
-#pragma unroll
-    for (int i = 0; i < kRtHidden; ++i) {
-        const float gi = g[i];
-        const float4* w = reinterpret_cast<const float4*>(W3T + i * kRtHidden);
-#pragma unroll
-        for (int q = 0; q < kRtBuckets / 4; ++q) {
-            const float4 v = w[q];
-            h[4 * q + 0] = fmaf(v.x, gi, h[4 * q + 0]);
-            h[4 * q + 1] = fmaf(v.y, gi, h[4 * q + 1]);
-            h[4 * q + 2] = fmaf(v.z, gi, h[4 * q + 2]);
-            h[4 * q + 3] = fmaf(v.w, gi, h[4 * q + 3]);
-        }
-    }
-    bk = 0;
-    bk2 = 1;
-    float mx = h[0], mx2 = h[1];
-    if (mx2 > mx) {
-        bk = 1;
-        bk2 = 0;
-        const float t = mx;
-        mx = mx2;
-        mx2 = t;
-    }
-#pragma unroll
-    for (int o = 2; o < kRtBuckets; ++o) {
-        if (h[o] > mx) {
-            mx2 = mx;
-            bk2 = bk;
-            mx = h[o];
-            bk = o;
-        } else if (h[o] > mx2) {
-            mx2 = h[o];
-            bk2 = o;
-        }
-    }
-}
-
-// Routed, certified search of one point for grid G (records in global memory).
-template <int DM>
-__device__ __noinline__ RouteOut<DM> route_search(const ForwardParams& p, const float* __restrict__ sP,
-                                                  const float* __restrict__ linv, const GridInfo& G, int gidx,
-                                                  const float (&v)[DM])
-{
-    RouteOut<DM> out;
-    out.cell = -1;
-    out.cands = 0;
-    const int d = p.d;
-    constexpr int F = Rec32<DM>::kFloats;
-    const float* recs = p.rec32 + G.roff * F;
-    float xh[DM], xs[DM], z[DM];
-    float A2 = 0.0f;
-#pragma unroll
-    for (int l = 0; l < DM; ++l) {
-        xh[l] = l < d ? __fsub_rn(v[l], G.mu[l]) : 0.0f;
-        xs[l] = -2.0f * xh[l];
-        A2 = __fmaf_rn(xh[l], xh[l], A2);
-    }
-#pragma unroll
-    for (int l = 0; l < DM; ++l) {
-        float a = 0.0f;
-#pragma unroll
-        for (int q = 0; q <= l; ++q)
-            if (l < d) a = fmaf(linv[l * d + q], xh[q], a);
-        z[l] = a;
-    }
-    const float A = __fsqrt_rn(A2);
-    // router
-    int bk, bk2;
-    mlp_route<DM>(sP, d, z, bk, bk2);
-    auto score = [&](int j) {
-        const float* r = recs + (long long)j * F;
-        float sc = __ldg(r);
-#pragma unroll
-        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(xs[l], __ldg(r + 1 + l), sc);
-        return sc;
-    };
-    // start cell: nearest member of the two most likely buckets
-    int i0 = -1;
-    float s0 = __int_as_float(0x7F800000);
-    for (int pass = 0; pass < 2; ++pass) {
-        const int b = pass == 0 ? bk : bk2;
-        const int bs = p.rt_bstart[b], be = p.rt_bstart[b + 1];
-        for (int t = bs; t < be; ++t) {
-            const int j = p.rt_members[t];
-            const float sc = score(j);
-            if (sc < s0) {
-                s0 = sc;
-                i0 = j;
-            }
-        }
-        out.cands += be - bs;
-    }
-    if (i0 < 0) return out;
-    // Elkan walk over the neighbours of i0
-    const float Eg = (float)(d + 2) * 0x1p-22f * (A + G.R) * (A + G.R);
-    auto rub = [&](float sc) { return __fsqrt_rn(fmaxf(sc + A2 + Eg, 0.0f)) * (1.0f + 0x1p-20f); };
-    const float r0 = rub(s0);
-    float B1 = s0, S = __int_as_float(0x7F800000), rs = r0;
-    int i1 = i0;
-    const long long base = ((long long)gidx * p.rt_N + i0) * p.rt_C;
-    // walk the neighbours in blocks of 8 independent loads, then test in order
-    constexpr int kW = 8;
-    int scanned = 0;                 // neighbours taken as candidates
-    bool stop = false;               // the distance bound was reached inside the list
-    for (int c = 0; c < p.rt_C && !stop; c += kW) {
-        float dl[kW], sc[kW];
-        int jj[kW];
-#pragma unroll
-        for (int q = 0; q < kW; ++q) {
-            const int cq = min(c + q, p.rt_C - 1);
-            dl[q] = __ldg(p.rt_nb_dist + base + cq);
-            jj[q] = __ldg(p.rt_nb_idx + base + cq);
-        }
-#pragma unroll
-        for (int q = 0; q < kW; ++q) sc[q] = score(jj[q]);
-#pragma unroll
-        for (int q = 0; q < kW; ++q) {
-            if (stop || c + q >= p.rt_C) continue;
-            if (dl[q] > (r0 + rs) * (1.0f + 0x1p-20f)) {
-                stop = true;
-                continue;
-            }
-            ++scanned;
-            if (sc[q] < B1) {
-                S = B1;
-                B1 = sc[q];
-                i1 = jj[q];
-                rs = rub(B1);
-            } else {
-                S = fminf(S, sc[q]);
-            }
-        }
-    }
-    const int c = scanned;
-    out.cands += c;
-    if (!stop) return out;          // list exhausted before the bound: exact fallback
-    const float* r = recs + (long long)i1 * F;
-    float n2 = 0.0f;
-#pragma unroll
-    for (int l = 0; l < DM; ++l) n2 = __fmaf_rn(r[1 + l], r[1 + l], n2);
-    if (screen_certified(d, A, B1, S, __fsqrt_rn(n2))) out.cell = i1;
-    return out;
-}
-
-template <int DM>
-__global__ void __launch_bounds__(128, 2) forward_router_kernel(const ForwardParams p)
-{
-    extern __shared__ __align__(16) float sP[];          // MLP parameters
-    __shared__ __align__(16) float s_linvA[DM * DM], s_linvB[DM * DM];
-    __shared__ long long s_item;
-    __shared__ LayerDesc s_L;
-    __shared__ GridInfo s_GA, s_GB;
-    __shared__ __align__(16) float s_pf[param_count(DM)];
-    __shared__ __align__(16) double s_pd[param_count(DM)];
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int d = p.d;
-    // transposed copy of the parameters: W1T[l][o], b1, W2T[i][o], b2, W3T[i][o], b3
-    {
-        const float* W1 = p.rt_params;
-        const float* b1 = W1 + kRtHidden * d;
-        const float* W2 = b1 + kRtHidden;
-        const float* b2 = W2 + kRtHidden * kRtHidden;
-        const float* W3 = b2 + kRtHidden;
-        const float* b3 = W3 + kRtHidden * kRtHidden;
-        float* T1 = sP;
-        float* tb1 = T1 + kRtHidden * d;
-        float* T2 = tb1 + kRtHidden;
-        float* tb2 = T2 + kRtHidden * kRtHidden;
-        float* T3 = tb2 + kRtHidden;
-        float* tb3 = T3 + kRtHidden * kRtHidden;
-        for (int e = tid; e < kRtHidden * d; e += blockDim.x) T1[(e % d) * kRtHidden + e / d] = W1[e];
-        for (int e = tid; e < kRtHidden * kRtHidden; e += blockDim.x) {
-            T2[(e % kRtHidden) * kRtHidden + e / kRtHidden] = W2[e];
-            T3[(e % kRtHidden) * kRtHidden + e / kRtHidden] = W3[e];
-        }
-        for (int e = tid; e < kRtHidden; e += blockDim.x) {
-            tb1[e] = b1[e];
-            tb2[e] = b2[e];
-            tb3[e] = b3[e];
-        }
-    }
-    __syncthreads();
-    // grids must be those the router was built for
-    if (p.status->spare[0] != p.rt_checksum) {
-        if (tid == 0) record_error(p.status, 1 /* QT_EINVAL */, 21);
-        return;
-    }
-    int cur = -1;
-    while (true) {
-        if (tid == 0) {
-            long long it = -1;
-            if (*((volatile int32_t*)&p.status->code) == 0) it = (long long)atomicAdd(&p.status->queue, 1ull);
-            s_item = it;
-        }
-        __syncthreads();
-        const long long item = s_item;
-        if (item < 0 || item >= p.total_items) break;
-        int k = (cur >= 0 && item >= s_L.item_begin && item < s_L.item_begin + s_L.items) ? cur : -1;
-        if (k < 0) {
-            int lo = 0, hi = p.n - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (p.layers[mid].item_begin <= item) lo = mid; else hi = mid - 1;
-            }
-            k = lo;
-        }
-        if (k != cur) {
-            __syncthreads();
-            if (tid == 0) {
-                s_L = p.layers[k];
-                s_GA = p.grids[s_L.gridA];
-                s_GB = p.grids[s_L.gridB];
-            }
-            const int pc = param_count(d);
-            for (int e = tid; e < pc; e += blockDim.x) {
-                s_pf[e] = p.params_f[(long long)k * p.params_stride + e];
-                s_pd[e] = p.params_d[(long long)k * p.params_stride + e];
-            }
-            for (int e = tid; e < d * d; e += blockDim.x) {
-                s_linvA[e] = p.rt_linv[(long long)k * d * d + e];
-                s_linvB[e] = p.rt_linv[(long long)(k + 1) * d * d + e];
-            }
-            __syncthreads();
-            cur = k;
-        }
-        const LayerDesc& L = s_L;
-        const unsigned long long ms = (unsigned long long)(item - L.item_begin) * blockDim.x + tid;
-        const bool valid = ms < p.M;
-        float X[DM], Y[DM];
-        pair_f32<DM>(s_pf, d, p.seed, k, valid ? ms : 0ull, X, Y);
-        int ci = 0, cj = 0, cand = 0;
-        bool needA = false, needB = false;
-        if (L.NA > 1) {
-            const RouteOut<DM> r = route_search<DM>(p, sP, s_linvA, s_GA, L.gridA, X);
-            ci = r.cell;
-            cand += r.cands;
-            needA = r.cell < 0 && valid;
-        }
-        if (L.NB > 1) {
-            const RouteOut<DM> r = route_search<DM>(p, sP, s_linvB, s_GB, L.gridB, Y);
-            cj = r.cell;
-            cand += r.cands;
-            needB = r.cell < 0 && valid;
-        }
-        // candidates per search (statistics)
-        int wc = valid ? cand : 0;
-        for (int off = 16; off >= 1; off >>= 1) wc += __shfl_xor_sync(0xFFFFFFFFu, wc, off);
-        if (lane == 0) atomicAdd(&p.status->candidates, (unsigned long long)wc);
-        // exact FP64 fallback
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            const bool need = g == 0 ? needA : needB;
-            unsigned mask = __ballot_sync(0xFFFFFFFFu, need);
-            if (!mask) continue;
-            double z[DM];
-#pragma unroll
-            for (int l = 0; l < DM; ++l) z[l] = (double)(g == 0 ? X[l] : Y[l]);
-            const GridInfo& G = g == 0 ? s_GA : s_GB;
-            // centred FP32 copy for the warp re-screen
-            float xs[DM];
-            float A2 = 0.0f;
-#pragma unroll
-            for (int l = 0; l < DM; ++l) {
-                const float xh = l < d ? __fsub_rn(g == 0 ? X[l] : Y[l], G.mu[l]) : 0.0f;
-                xs[l] = -2.0f * xh;
-                A2 = __fmaf_rn(xh, xh, A2);
-            }
-            const float A = __fsqrt_rn(A2);
-            while (mask) {
-                const int src = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const int r = warp_window_nn<DM>(xs, A, z, src, p.rec32 + G.roff * Rec32<DM>::kFloats, G.Npad,
-                                                 p.g64 + G.goff * d, G.N, d);
-                if (lane == src) {
-                    if (g == 0) ci = r; else cj = r;
-                }
-                if (lane == 0) atomicAdd(&p.status->rechecks, 1ull);
-            }
-        }
-        if (valid) {
-            if ((unsigned)ci >= (unsigned)L.NA || (unsigned)cj >= (unsigned)L.NB) {
-                record_error(p.status, 6 /* QT_EDEVICE */, 22);
-            } else {
-                count_add(p.counts, p.counts_u32, L.coff + (long long)ci * L.NB + cj, 1u);
-                if (p.dump_count > 0 && (ms % (unsigned long long)p.dump_stride) == 0ull) {
-                    const unsigned long long t = ms / (unsigned long long)p.dump_stride;
-                    if (t < (unsigned long long)p.dump_count) {
-                        const long long row = (long long)k * p.dump_count + (long long)t;
-                        for (int l = 0; l < d; ++l) {
-                            p.dumpX[row * d + l] = (double)X[l];
-                            p.dumpY[row * d + l] = (double)Y[l];
-                        }
-                        p.dumpI[row] = ci;
-                        p.dumpJ[row] = cj;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
-template <int DM>
-static cudaError_t launch_rt(const ForwardParams& p, int num_sms, int* bps, cudaStream_t st)
-{
-    auto kern = forward_router_kernel<DM>;
-    const int dyn = rt_param_count(p.d) * 4;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-    if (e != cudaSuccess) return e;
-    int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 128, dyn);
-    if (e != cudaSuccess) return e;
-    if (b < 1) return cudaErrorInvalidConfiguration;
-    *bps = b;
-    long long grid = (long long)num_sms * b;
-    if (grid > p.total_items) grid = p.total_items;
-    kern<<<(unsigned)grid, 128, dyn, st>>>(p);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_router_forward(int dm, const ForwardParams& p, int num_sms, int* bps, cudaStream_t st)
-{
-    if (dm == 2) return launch_rt<2>(p, num_sms, bps, st);
-    if (dm == 4) return launch_rt<4>(p, num_sms, bps, st);
-    if (dm == 6) return launch_rt<6>(p, num_sms, bps, st);
-    if (dm == 8) return launch_rt<8>(p, num_sms, bps, st);
-    if (dm == 10) return launch_rt<10>(p, num_sms, bps, st);
-    if (dm == 12) return launch_rt<12>(p, num_sms, bps, st);
-    if (dm == 16) return launch_rt<16>(p, num_sms, bps, st);
-    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_grid_checksum(const double* grids, long long count, unsigned long long* out, cudaStream_t st)

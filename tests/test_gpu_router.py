@@ -111,3 +111,19 @@ def test_router_fused_backward_price(ctx, B, ar8_case):
     assert p1 == p0
     ref = oracle.price(model.N, oracle.transitions(model, g, model.M, model.seed, oracle.PREC_F32), phi)
     assert abs(p1 - ref) <= 1e-12 * abs(ref)
+
+
+def test_router_timeout_is_reported(ctx, B, ar8_case):
+    """A wait for the router network's tensor-core layers that gives up is
+    reported as a timeout, and the next call on the same context is exact."""
+    model, g, gd, trained, _ = ar8_case
+    with pytest.raises(B.QtError) as e:
+        ctx.transitions(model, gd, model.M, model.seed,
+                        B.options(form=B.FORM_ROUTER_CERT, router=trained.handle, spin_budget=-1))
+    assert e.value.status == B.QT_ETIMEOUT
+    counts, _, _ = ctx.transitions(model, gd, model.M, model.seed,
+                                   B.options(form=B.FORM_ROUTER_CERT, router=trained.handle))
+    ref = oracle.transitions(model, g, model.M, model.seed, oracle.PREC_F32)
+    got = B.split_counts(model.N, counts.cpu().numpy())
+    for k in range(model.n):
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=f"layer {k}")
