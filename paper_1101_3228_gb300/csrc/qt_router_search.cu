@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "../../include/qt.h"
 #include "qt_forward_tc.cuh"
 #include "qt_launch.h"
@@ -545,11 +547,25 @@ cudaError_t launch_rt(const ForwardParams& p, int num_sms, int* bps, cudaStream_
     const int dyn = kRtDynSmem;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
-    int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kRtRows, dyn);
+    // CTAs per SM from the kernel's registers and shared memory (the runtime's
+    // occupancy query answers 1 for this kernel, although four fit), at most
+    // as many as share the SM's 512 tensor-memory columns
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
-    // every resident CTA holds kRtTmemCols of the SM's 512 tensor-memory columns
-    if (b < 1 || b * (int)kRtTmemCols > 512) return cudaErrorInvalidConfiguration;
+    int dev = 0, regs_sm = 0, smem_sm = 0, smem_rsv = 0, thr_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) != cudaSuccess)
+        return e;
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;          // registers are granted per warp
+    int b = 512 / (int)kRtTmemCols;
+    b = std::min(b, regs_sm / (warp_regs * (kRtRows / 32)));
+    b = std::min(b, smem_sm / (int)(dyn + fa.sharedSizeBytes + smem_rsv));
+    b = std::min(b, thr_sm / kRtRows);
+    if (b < 1) return cudaErrorInvalidConfiguration;
     *bps = b;
     long long grid = (long long)num_sms * b;
     if (grid > p.total_items) grid = p.total_items;
