@@ -482,8 +482,13 @@ def main():
     pform = plain_form(model, B)
     if args.plain_steps > 0 and pform != form:
         po = B.options(form=pform, prec=prec, counts_type=ctype)
-        pms, _, _ = timed_steps(ctx, lambda: step(po), args.plain_steps, 1, flush, stream, dist)
+        pms, pkern, _ = timed_steps(ctx, lambda: step(po), args.plain_steps, 1, flush, stream, dist)
         plain = {"form": B.FORM_NAMES[pform], "value": world * units / (pms / 1e3), "ms_per_step": pms}
+        if pform == B.FORM_F32_RECHECK:
+            pk = statistics.mean(pkern) if pkern and all(k > 0 for k in pkern) else pms
+            n_sm_p = torch.cuda.get_device_properties(dev).multi_processor_count
+            pk_peaks = json.load(open(MEASURED)) if os.path.exists(MEASURED) else {}
+            plain["roofline"] = alu_roofline(model, units, pk, pk_peaks, n_sm_p)
 
     # end to end through the public API: host grids and payoff in, price out
     del counts
