@@ -127,3 +127,25 @@ def test_router_timeout_is_reported(ctx, B, ar8_case):
     got = B.split_counts(model.N, counts.cpu().numpy())
     for k in range(model.n):
         np.testing.assert_array_equal(got[k], ref[k], err_msg=f"layer {k}")
+
+
+@pytest.mark.parametrize("d", [2, 5, 16])
+def test_router_counts_bit_exact_across_dimension_classes(ctx, B, d):
+    """The tensor-core inference builds its first-layer rows from the whitened
+    coordinates zero-padded to 16 columns: d = 2 and 5 leave padding in the
+    dimension classes 2 and 6, d = 16 fills every column.  Counts bit-exact
+    against the oracle in each case."""
+    model = W._ar_model(f"ar{d}", d, 2, 256, 3001, "basket_put", 1.0, 9)
+    g = W.layer_grids(model, samples=8000, iters=3)
+    gd = _dev(g)
+    rt = ctx.router_train(model, gd, samples=20000, layers=2, epochs=3)
+    try:
+        counts, stats, _ = ctx.transitions(model, gd, model.M, model.seed,
+                                           B.options(form=B.FORM_ROUTER_CERT, router=rt.handle))
+    finally:
+        rt.close()
+    ref = oracle.transitions(model, g, model.M, model.seed, oracle.PREC_F32)
+    got = B.split_counts(model.N, counts.cpu().numpy())
+    for k in range(model.n):
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=f"d={d} layer {k}")
+    assert stats.form_used == B.FORM_ROUTER_CERT and stats.device_status == 0
