@@ -322,29 +322,59 @@ __device__ __forceinline__ void resolve_init(ResolveState<S>& rs)
 }
 
 // Re-score local chunk lc of `recs` (global chunk gc) for one sample: lowest
-// index achieving B1, smallest other score of the chunk, norm of the best record.
+// index achieving B1, smallest other score of the chunk, norm of the best
+// record.  Chunks are 16 records apart, which puts record q of every chunk in
+// the same shared-memory banks; lane t therefore starts at record t mod 16 and
+// wraps around, so that lanes whose best chunks differ read different banks
+// (one vector load per 16 bytes of a record).  The outcome does not depend on
+// the order: the lowest index whose score equals B1, and as the other score the
+// smallest score of the rest (B1 itself when two records reach it).
 template <int DM>
 __device__ __forceinline__ void resolve_chunk(const float* __restrict__ recs, int lc, int gc, const float (&x)[DM],
                                               float B1, int& idx, float& S1, float& r1)
 {
     constexpr int F = Rec32<DM>::kFloats;
-    idx = -1;
-    S1 = __int_as_float(0x7F800000);
-    r1 = 0.0f;
-    for (int q = 0; q < kChunk; ++q) {
-        const float* r = recs + (lc * kChunk + q) * F;
-        float sc = r[0];
+    constexpr int V = F / 4;
+    const int rot = (int)(threadIdx.x & (kChunk - 1));
+    const float4* base = reinterpret_cast<const float4*>(recs) + (long long)lc * kChunk * V;
+    auto load = [&](int q, float (&f)[F]) {
 #pragma unroll
-        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], r[1 + l], sc);
-        if (sc == B1 && idx < 0) {
-            idx = gc * kChunk + q;
-            float n2 = 0.0f;
-#pragma unroll
-            for (int l = 0; l < DM; ++l) n2 = __fmaf_rn(r[1 + l], r[1 + l], n2);
-            r1 = __fsqrt_rn(n2);
-        } else {
-            S1 = fminf(S1, sc);
+        for (int v = 0; v < V; ++v) {
+            const float4 a = base[q * V + v];
+            f[4 * v] = a.x;
+            f[4 * v + 1] = a.y;
+            f[4 * v + 2] = a.z;
+            f[4 * v + 3] = a.w;
         }
+    };
+    int lo = kChunk, matches = 0;
+    float other = __int_as_float(0x7F800000);
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+        const int q = (u + rot) & (kChunk - 1);
+        float f[F];
+        load(q, f);
+        float sc = f[0];
+#pragma unroll
+        for (int l = 0; l < DM; ++l) sc = __fmaf_rn(x[l], f[1 + l], sc);
+        if (sc == B1) {
+            ++matches;
+            lo = min(lo, q);
+        } else {
+            other = fminf(other, sc);
+        }
+    }
+    S1 = matches >= 2 ? fminf(other, B1) : other;
+    idx = -1;
+    r1 = 0.0f;
+    if (lo < kChunk) {
+        idx = gc * kChunk + lo;
+        float f[F];
+        load(lo, f);
+        float n2 = 0.0f;
+#pragma unroll
+        for (int l = 0; l < DM; ++l) n2 = __fmaf_rn(f[1 + l], f[1 + l], n2);
+        r1 = __fsqrt_rn(n2);
     }
 }
 
