@@ -298,19 +298,23 @@ QT_API qt_status qt_transitions_workspace(const qt_model* model, const qt_option
  * best distance found so far) finds the exact cell from any start cell i0.
  * The router (an MLP d -> 64 -> 64 -> 64, ReLU, on whitened coordinates
  * L_k^{-1}(x - m_k)) predicts which of 64 buckets (a k-means partition of the
- * grid points) holds the cell; the start cell is the nearest member of that
- * bucket.  A wrong prediction costs time, never exactness.
- * Requires N_k equal for all k >= 1 (one bucket partition serves every layer)
- * and 64 <= N_k <= 65535.                                                     */
+ * grid points) holds the cell; the start cell is the nearest member of the two
+ * most likely buckets.  Training runs in FP32 on the CUDA cores; the search
+ * evaluates the network on the tensor cores (FP16 operands, FP32 accumulators,
+ * 128 samples per tile).  A wrong prediction, or a rounding of the FP16
+ * inference, costs time, never exactness.
+ * Requires N_k equal for all k >= 1 (one bucket partition serves every layer),
+ * 64 <= N_k <= 8192 and d <= 16.                                              */
 typedef struct qt_router qt_router;
 
 typedef struct {
     int64_t train_samples;   /* labelled (sample, exact cell) pairs; 0 = 10^6            */
     int32_t train_layers;    /* layers the pairs are drawn from (evenly spaced); 0 = 8    */
-    int32_t epochs;          /* passes over the pairs; 0 = 4                               */
+    int32_t epochs;          /* passes over the pairs; 0 = 8                               */
     int32_t batch;           /* minibatch; 0 = 4096                                        */
-    int32_t neighbours;      /* sorted neighbours kept per grid point (Elkan list); 0 = 256 */
-    float lr;                /* Adam step; 0 = 2e-3                                        */
+    int32_t neighbours;      /* sorted neighbours kept per grid point (Elkan list); 0 = 1024,
+                                at most N_k - 1                                            */
+    float lr;                /* Adam step; 0 = 3e-3                                        */
     int32_t untrained;       /* 1: keep the seeded initial weights (for comparisons)       */
     int32_t reserved[3];
 } qt_router_config;
