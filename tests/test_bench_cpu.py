@@ -32,7 +32,7 @@ def test_rooflines_are_work_over_time_over_peak():
     r = bench.tensor_roofline(m8, units, 4000.0, peaks)
     assert abs(r["achieved"] - (4001 + 49 * 8000) / 50 * 16 * units / 4.0 / 1e12) < 1e-9 * r["achieved"]
     assert abs(r["frac"] - r["achieved"] / 1700.0) < 1e-15
-    assert abs(r["mma_frac"] / r["frac"] - 2.0) < 1e-12          # K = 32 columns against 2d = 16
+    assert abs(r["mma_frac"] / r["frac"] - 4.0) < 1e-12          # 2K = 64 pipe flops against 2d = 16
     a = bench.alu_roofline(m8, units, 4000.0, peaks, 152)
     assert abs(a["peak"] - 152 * 128 * 2 * 2000.0e6 / 1e12) < 1e-12
     assert abs(a["frac"] - a["achieved"] / a["peak"]) < 1e-15
